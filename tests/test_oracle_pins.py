@@ -1,0 +1,364 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the planted mistake it is meant to catch. None compares the
+oracle with a retyped copy of itself: the expected values come from closed
+forms (Zel'dovich plane wave, textbook F_2/G_2), brute-force mode sums with the
+independent Fourier-kernel recursion, published known-answer vectors,
+invariants (mass conservation, Hermitian symmetry, exact 2^n scaling, zero
+padding) or an independent quadrature.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import cosmology, estimators, kernels, rng, spt
+from tests import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ generator
+def test_philox_known_answers():
+    """Published Philox4x32-10 vectors (catches a wrong constant, word order or round count)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(v, 16) for v in r]
+        out = rng.philox4x32_10(np.array(vals[0:4]), np.array(vals[4:6]))
+        assert [int(v) for v in out] == vals[6:10]
+
+
+def test_mode_key_two_complement():
+    lo, hi = rng.mode_key(np.array([-1]), np.array([0]), np.array([1]))
+    packed = int(lo[0]) | (int(hi[0]) << 32)
+    assert packed & 0x1FFFFF == 0x1FFFFF          # -1 in 21-bit two's complement
+    assert (packed >> 21) & 0x1FFFFF == 0
+    assert (packed >> 42) & 0x1FFFFF == 1
+
+
+# ------------------------------------------------------------- DFT convention
+def test_transform_pair_matches_naive_sums():
+    """Sec. II.C transform pair against the triple sums written out
+    (catches a sign flip or a missing 1/N^3)."""
+    N = 6
+    a_k = inputs.random_complex((N, N, N), 1)
+    j = np.arange(N)
+    ph = np.exp(2j * math.pi * np.outer(j, j) / N)  # e^{+i k x}, [x, k]
+    naive_x = np.einsum("xa,yb,zc,abc->xyz", ph, ph, ph, a_k)
+    assert np.allclose(spt.backward(a_k), naive_x, rtol=0, atol=1e-12 * np.abs(naive_x).max())
+    a_x = inputs.random_complex((N, N, N), 2)
+    naive_k = np.einsum("xa,yb,zc,xyz->abc", ph.conj(), ph.conj(), ph.conj(), a_x) / N ** 3
+    assert np.allclose(spt.forward(a_x), naive_k, rtol=0, atol=1e-12 * np.abs(naive_k).max())
+
+
+# ------------------------------------------------------------------ cosmology
+def test_sigma8_normalisation_by_independent_quadrature():
+    """sigma_8 of the normalised spectrum by adaptive quadrature in k (not the
+    oracle's Simpson in ln k): catches a wrong window, measure or 2 pi^2."""
+    c = dict(cosmology.DEFAULT_COSMO)
+    A = cosmology.amplitude(c)
+    R = 8.0
+
+    def integrand(k):
+        x = k * R
+        w = 3.0 * (math.sin(x) - x * math.cos(x)) / x ** 3 if x > 1e-3 else 1.0
+        return k * k * float(cosmology.linear_pk(np.array([k]), c, A)[0]) * w * w
+
+    pts = [1e-3, 1e-2, 0.05, 0.1, 0.3, 1.0, 3.0, 10.0]
+    total = 0.0
+    edges = [1e-6] + pts + [200.0]
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        total += integrate.quad(integrand, lo, hi, limit=400, epsabs=0, epsrel=1e-11)[0]
+    sigma8 = math.sqrt(total / (2 * math.pi ** 2))
+    assert abs(sigma8 - 0.8) < 1e-6
+
+
+def test_bbks_limits():
+    """T -> 1 with slope -(2.34/2 + 3.89/4) at q -> 0; T q^2 / ln(2.34 q) ->
+    1 / (2.34 * 6.71) at q -> inf (catches a wrong coefficient in either end)."""
+    q = np.array([1e-6])
+    slope = (cosmology.bbks_transfer(q)[0] - 1.0) / q[0]
+    assert abs(slope + (1.17 + 3.89 / 4)) < 1e-4
+    q = np.array([1e9])
+    lim = cosmology.bbks_transfer(q)[0] * q[0] ** 2 / math.log(2.34 * q[0])
+    assert abs(lim * 2.34 * 6.71 - 1.0) < 1e-2
+
+
+# ---------------------------------------------------------- initial field
+def test_linear_field_hermitian_cut_and_real():
+    N, L, n_max = 24, 300.0, 3
+    d = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed=11)
+    idx = (-np.arange(N)) % N
+    assert np.array_equal(d, np.conj(d[idx][:, idx][:, :, idx]))
+    assert d[0, 0, 0] == 0
+    assert not np.any(d[spt.nyquist_mask(N)])
+    sx, sy, sz = spt.wave_indices(N)
+    s2 = sx ** 2 + sy ** 2 + sz ** 2
+    r = N / (n_max + 1)
+    assert not np.any(d[s2 > r * r])
+    assert np.all(d[(s2 <= r * r) & (s2 > 0)] != 0)
+    x = spt.backward(d)
+    assert np.abs(x.imag).max() < 1e-12 * np.abs(x.real).max()
+
+
+def test_linear_field_gaussian_statistics():
+    """L^3 |delta|^2 / P(k) has mean 1 and Re/Im parts are N(0, 1/2) after
+    normalising: catches a missing 1/sqrt(2), L^3 or a wrong Box-Muller."""
+    N, L, n_max = 48, 500.0, 1
+    c = cosmology.DEFAULT_COSMO
+    d = spt.linear_field(N, L, n_max, c, seed=3)
+    k, s2 = estimators.mode_k(N, L)
+    sel = (d != 0)
+    ratio = L ** 3 * np.abs(d[sel]) ** 2 / cosmology.linear_pk(k[sel], c)
+    n = ratio.size // 2  # pairs are not independent
+    assert abs(ratio.mean() - 1.0) < 5.0 / math.sqrt(n)
+    z = d[sel] / np.sqrt(cosmology.linear_pk(k[sel], c) / L ** 3)
+    assert abs(z.real.std() ** 2 - 0.5) < 5 * 0.5 * math.sqrt(2.0 / n)
+    assert abs(z.real.mean()) < 5 * math.sqrt(0.5 / n)
+
+
+def test_linear_field_shared_modes_across_grids():
+    """Keying by wavevector: the same seed and box on N and 2N share the
+    common in-band modes exactly."""
+    c = cosmology.DEFAULT_COSMO
+    a = spt.linear_field(16, 200.0, 3, c, seed=5, kcut_lin=2 * math.pi / 200.0 * 3.5)
+    b = spt.linear_field(32, 200.0, 3, c, seed=5, kcut_lin=2 * math.pi / 200.0 * 3.5)
+    s = spt.signed_index(16)
+    ii = s % 32
+    assert np.array_equal(a, b[np.ix_(ii, ii, ii)])
+
+
+# ------------------------------------------------------- recursion pins
+def test_single_plane_wave_all_orders():
+    """1D wave: planar SPT is Zel'dovich; delta_n(+-m k_F) =
+    (-1)^j m^n (A/2)^n / (j! (m+j)!), n = m + 2j, theta_n = delta_n, zero
+    elsewhere. Catches a wrong recursion coefficient or a dropped term at any order."""
+    N, L, A = 16, 100.0, 0.1
+    d1 = inputs.plane_waves(N, [((1, 0, 0), A)])
+    dk, tk = spt.run_orders(d1, L, 5)
+    for n in range(1, 6):
+        exp = np.zeros((N, N, N))
+        for m in range(n % 2, n + 1, 2):
+            j = (n - m) // 2
+            v = (-1) ** j * m ** n * (A / 2) ** n / (math.factorial(j) * math.factorial(m + j))
+            exp[m % N, 0, 0] = v
+            exp[-m % N, 0, 0] = v
+        scale = (A / 2) ** n
+        assert np.abs(dk[n] - exp).max() < 1e-12 * scale, n
+        assert np.abs(tk[n] - exp).max() < 1e-12 * scale, n
+
+
+def test_fourier_recursion_reduces_to_textbook_f2():
+    g = inputs.rng(4)
+    for _ in range(20):
+        q1, q2 = g.standard_normal(3), g.standard_normal(3)
+        F, G = kernels.fg_sym(q1, q2)
+        Fc, Gc = kernels.f2_closed(q1, q2)
+        assert abs(F - Fc) < 1e-13 and abs(G - Gc) < 1e-13
+
+
+def test_two_plane_waves_second_order():
+    """delta_2(k1+k2) = F_2 A1 A2 / 2 and theta_2 = G_2 A1 A2 / 2 with the
+    textbook F_2, G_2; also k1-k2 and 2 k1 (catches a transposed tensor index
+    or a sign error in u = -i k theta / k^2)."""
+    N, L = 16, 200.0
+    kF = 2 * math.pi / L
+    s1, s2 = np.array([1, 0, 0]), np.array([1, 2, 0])
+    A1, A2 = 0.07, 0.05
+    d1 = inputs.plane_waves(N, [(tuple(s1), A1), (tuple(s2), A2)])
+    dk, tk = spt.run_orders(d1, L, 2)
+    for t, (qa, qb), amp in [(s1 + s2, (s1, s2), A1 * A2 / 2), (s1 - s2, (s1, -s2), A1 * A2 / 2),
+                             (2 * s1, (s1, s1), A1 * A1 / 4)]:
+        F, G = kernels.f2_closed(kF * qa, kF * qb)
+        idx = tuple(int(c) % N for c in t)
+        assert abs(dk[2][idx] - F * amp) < 1e-14
+        assert abs(tk[2][idx] - G * amp) < 1e-14
+
+
+def _mode_sum(d1, L, order, kernel_index):
+    """Brute-force delta_n(k) (or theta_n) = sum over ordered n-tuples of nonzero
+    linear modes of F_n^s(q_1..q_n) prod delta_1(q_i), for sparse delta_1."""
+    N = d1.shape[0]
+    kF = 2 * math.pi / L
+    nz = np.argwhere(d1 != 0)
+    s = spt.signed_index(N)
+    out = {}
+    for tup in itertools.product(range(len(nz)), repeat=order):
+        qs = [kF * np.array([s[c] for c in nz[i]], float) for i in tup]
+        tot = sum(np.array([s[c] for c in nz[i]]) for i in tup)
+        fg = kernels.fg_sym(*qs)[kernel_index]
+        val = fg * np.prod([d1[tuple(nz[i])] for i in tup])
+        key = tuple(int(c) for c in tot)
+        out[key] = out.get(key, 0) + val
+    return out
+
+
+def test_three_plane_waves_third_order_mode_sum():
+    """delta_3 and theta_3 at every mode equal the ordered triple mode sum with
+    the symmetrised F_3 / G_3 of the Fourier recursion (no aliasing at N=24)."""
+    N, L = 24, 300.0
+    d1 = inputs.plane_waves(N, [((1, 0, 0), 0.05), ((1, 1, 0), 0.04), ((0, 1, 2), 0.03)])
+    dk, tk = spt.run_orders(d1, L, 3)
+    for which, arr in [(0, dk[3]), (1, tk[3])]:
+        exp = _mode_sum(d1, L, 3, which)
+        got_max = 0.0
+        full = np.zeros_like(arr)
+        for key, v in exp.items():
+            full[tuple(c % N for c in key)] += v
+        scale = np.abs(full).max()
+        assert np.abs(arr - full).max() < 1e-12 * scale
+        got_max = np.abs(arr).max()
+        assert got_max > 0
+
+
+def test_random_field_second_order_mode_sum():
+    """Random band-limited delta_1 on 12^3: grid delta_2 equals the pair mode sum
+    with textbook F_2 at every mode |k| < K_c (exact in band)."""
+    N, L, n_max = 12, 150.0, 3
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed=21)
+    dk, tk = spt.run_orders(d1, L, 2)
+    kF = 2 * math.pi / L
+    s = spt.signed_index(N)
+    nz = np.argwhere(d1 != 0)
+    qv = np.array([[s[c] for c in p] for p in nz])
+    amp = np.array([d1[tuple(p)] for p in nz])
+    r = N / (n_max + 1)
+    expF = {}
+    expG = {}
+    for i in range(len(nz)):
+        for j in range(len(nz)):
+            t = qv[i] + qv[j]
+            if t @ t >= r * r:
+                continue
+            key = tuple(int(c) for c in t)
+            if not np.any(qv[i] + qv[j]):
+                F = G = 0.0   # F_2(q, -q) = G_2(q, -q) = 0
+            else:
+                F, G = kernels.f2_closed(kF * qv[i], kF * qv[j])
+            expF[key] = expF.get(key, 0) + F * amp[i] * amp[j]
+            expG[key] = expG.get(key, 0) + G * amp[i] * amp[j]
+    scale = np.abs(dk[2]).max()
+    for key in expF:
+        idx = tuple(c % N for c in key)
+        assert abs(dk[2][idx] - expF[key]) < 1e-12 * scale
+        assert abs(tk[2][idx] - expG[key]) < 1e-12 * scale
+
+
+# ------------------------------------------------------------- invariants
+@pytest.fixture(scope="module")
+def random_orders():
+    N, L, n_max = 16, 200.0, 5
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed=8)
+    return N, L, n_max, d1, spt.run_orders(d1, L, n_max)
+
+
+def test_mass_conservation_every_order(random_orders):
+    N, L, n_max, d1, (dk, tk) = random_orders
+    for n in range(2, n_max + 1):
+        scale = np.abs(dk[n]).max()
+        assert abs(dk[n][0, 0, 0]) < 1e-12 * scale
+        assert abs(tk[n][0, 0, 0]) < 1e-12 * scale
+
+
+def test_hermitian_every_order(random_orders):
+    N, L, n_max, d1, (dk, tk) = random_orders
+    idx = (-np.arange(N)) % N
+    for n in range(2, n_max + 1):
+        for a in (dk[n], tk[n]):
+            mirror = np.conj(a[idx][:, idx][:, :, idx])
+            assert np.abs(a - mirror).max() < 1e-13 * np.abs(a).max()
+
+
+def test_exact_power_of_two_scaling(random_orders):
+    """delta_1 -> 2 delta_1 gives delta_n -> 2^n delta_n bit for bit (Sec. II.B
+    growth-factor expansion: delta_n scales as D_+^n)."""
+    N, L, n_max, d1, (dk, tk) = random_orders
+    dk2, tk2 = spt.run_orders(2.0 * d1, L, n_max)
+    for n in range(2, n_max + 1):
+        assert np.array_equal(dk2[n], 2.0 ** n * dk[n])
+        assert np.array_equal(tk2[n], 2.0 ** n * tk[n])
+
+
+def test_zero_padding_invariance_in_band():
+    """The same band-limited delta_1 on 12^3 and on the 4x zero-padded 48^3 grid
+    gives equal delta_n, theta_n at every |k| < K_c (alias cut is exact in band)."""
+    N, L, n_max = 12, 150.0, 5
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed=17)
+    big = np.zeros((4 * N,) * 3, dtype=complex)
+    s = spt.signed_index(N)
+    ii = s % (4 * N)
+    big[np.ix_(ii, ii, ii)] = d1
+    dk, tk = spt.run_orders(d1, L, n_max)
+    dkb, tkb = spt.run_orders(big, L, n_max)
+    sx, sy, sz = spt.wave_indices(N)
+    band = (sx ** 2 + sy ** 2 + sz ** 2) < (N / (n_max + 1)) ** 2
+    for n in range(2, n_max + 1):
+        small = dk[n][band]
+        large = dkb[n][np.ix_(ii, ii, ii)][band]
+        assert np.abs(small - large).max() < 1e-10 * np.abs(large).max(), n
+        small = tk[n][band]
+        large = tkb[n][np.ix_(ii, ii, ii)][band]
+        assert np.abs(small - large).max() < 1e-10 * np.abs(large).max(), n
+
+
+def test_translation_covariance():
+    """delta_1(k) e^{-i k.d} -> delta_n(k) e^{-i k.d} for a grid shift d."""
+    N, L, n_max = 12, 150.0, 4
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed=2)
+    sx, sy, sz = spt.wave_indices(N)
+    ph = np.exp(-2j * math.pi * (2 * sx + 5 * sy - 3 * sz) / N)
+    dk, _ = spt.run_orders(d1, L, n_max)
+    dks, _ = spt.run_orders(d1 * ph, L, n_max)
+    for n in range(2, n_max + 1):
+        assert np.abs(dks[n] - dk[n] * ph).max() < 1e-12 * np.abs(dk[n]).max()
+
+
+# ------------------------------------------------------------- estimators
+def test_power_on_hand_built_spectrum():
+    """A spectrum with a(k) = sqrt(c_i / L^3) on shell i (and b = a) gives
+    P = c_i and N_k equal to a direct count of integer vectors."""
+    N, L = 16, 100.0
+    kF = 2 * math.pi / L
+    edges = [kF * (b + 0.5) for b in range(6)]
+    vals = [3.0, 5.0, 7.0, 11.0, 13.0]
+    sx, sy, sz = spt.wave_indices(N)
+    r = np.sqrt(sx ** 2 + sy ** 2 + sz ** 2)
+    a = np.zeros((N, N, N), complex)
+    for i, v in enumerate(vals):
+        a[(r >= i + 0.5) & (r < i + 1.5)] = math.sqrt(v / L ** 3)
+    p, nk = estimators.power(a, a, L, edges)
+    assert np.allclose(p, vals, rtol=1e-14)
+    for i in range(5):
+        cnt = sum(1 for x in range(-8, 8) for y in range(-8, 8) for z in range(-8, 8)
+                  if (i + 0.5) ** 2 <= x * x + y * y + z * z < (i + 1.5) ** 2)
+        assert nk[i] == cnt
+    # cross term: Re part only
+    b = 1j * a
+    p2, _ = estimators.power(a, b, L, edges)
+    assert np.abs(p2).max() < 1e-14
+
+
+def test_bispectrum_fft_estimator_equals_triangle_enumeration():
+    N, L = 12, 120.0
+    kF = 2 * math.pi / L
+    a = spt.linear_field(N, L, 3, cosmology.DEFAULT_COSMO, seed=31)
+    b = spt.linear_field(N, L, 3, cosmology.DEFAULT_COSMO, seed=32)
+    edges = [kF * e for e in (0.5, 1.5, 2.5, 3.5)]
+    E, nt = estimators.bispectrum_equilateral(a, b, L, edges)
+    Eb, ntb = estimators.bispectrum_brute(a, b, L, edges)
+    assert np.allclose(nt, ntb, rtol=1e-12, atol=1e-9)
+    assert np.allclose(E, Eb, rtol=1e-10, atol=0)
+    # independent count of closed ordered triangles of integer vectors per shell
+    for i in range(3):
+        lo, hi = (i + 0.5) ** 2, (i + 1.5) ** 2
+        vecs = [(x, y, z) for x in range(-5, 6) for y in range(-5, 6) for z in range(-5, 6)
+                if lo <= x * x + y * y + z * z < hi]
+        vs = set(vecs)
+        cnt = sum(1 for p in vecs for q in vecs
+                  if (-(p[0] + q[0]), -(p[1] + q[1]), -(p[2] + q[2])) in vs)
+        assert round(nt[i]) == cnt
