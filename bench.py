@@ -1,0 +1,292 @@
+"""Throughput benchmark of the GridSPT hot path on GB300.
+
+Workload: 16 realisations of a 512^3 grid, L = 2000 Mpc/h, n_max = 5, FP32
+fields (BBKS LCDM, Omega_m = 0.3, h = 0.7, n_s = 0.96, sigma_8 = 0.8, seeds
+1000 + r). One step = for every realisation of the batch: Gaussian initial
+field, orders 2..5 of the recursion, the six P-terms P11, P13, P22, P15, P24,
+P33 in 32 log bins over 0.01-0.4 h/Mpc, and the tree-level equilateral
+bispectrum in 16 shells over [0, K_c). Metric: Mcells*orders/s =
+batch * N^3 * n_max / step time. Every field (512 MiB) is larger than the
+129 MB L2, so no L2 flush is needed between steps.
+
+`--impl reference` times the FP64 CPU oracle instead (bounded sample, see
+cpu_baseline). Under torchrun each rank runs its own realisations (replicas:
+no data exchange) and rank 0 reports the aggregate.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcells*orders/s to 5th order at 512^3 FP32"
+UNIT = "Mcells*orders/s"
+N_GRID, BOX, N_MAX = 512, 2000.0, 5
+FALLBACK_HBM_GBS = 6800.0
+# bytes per launch from the last ncu capture of the dominant kernel (None until taken
+# for the current kernel source)
+NCU_TRAFFIC = {}
+
+
+def log_edges(lo, hi, nb):
+    return [lo * (hi / lo) ** (i / nb) for i in range(nb + 1)]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if key in d:
+                    return float(d[key]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle arm
+def oracle_sample(target_s=12.0):
+    """FP64 oracle on a bounded sample of the workload: one realisation of a
+    64^3 grid with the same cell size (L = 250 Mpc/h), orders 1..5 (initial
+    field + recursion), repeated until about target_s seconds of CPU work."""
+    import numpy as np  # noqa: F401
+    from oracle import cosmology, spt
+    n, L = 64, BOX * 64 / N_GRID
+    A = cosmology.amplitude(cosmology.DEFAULT_COSMO)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        d1 = spt.linear_field(n, L, N_MAX, cosmology.DEFAULT_COSMO, 1000 + reps, A=A)
+        spt.run_orders(d1, L, N_MAX)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    value = reps * n ** 3 * N_MAX / el / 1e6
+    return value, el, reps, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{reps} realisation(s) of 64^3, L=250 Mpc/h (same cell size), n_max=5, "
+                                       f"IC + recursion, numpy FP64 single thread, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(target_s=0.0)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, el, reps, cb = oracle_sample(target_s=max(1.0, 30.0 / max(args.steps, 1)))
+        vals.append(v)
+    total = time.perf_counter() - t_all
+    value = statistics.median(vals)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "gridspt-64^3-L250-nmax5 (bounded oracle sample of "
+                                                        "gridspt-512^3-L2000-nmax5)"},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1807_04215_gb300 import gridspt as g
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    N, B = args.n, args.batch
+    L = BOX * N / N_GRID
+    plan = g.Plan(N, N_MAX, L, batch=B)
+    seeds = [1000 + rank * B + r for r in range(B)]
+    d1 = torch.empty(plan.half_shape(B), dtype=torch.complex64, device="cuda")
+    spectra = torch.empty(plan.half_shape(B, N_MAX - 1, 2), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device="cuda")
+    pedges = log_edges(0.01, 0.4, 32)
+    kc = 2 * math.pi / L * N / (N_MAX + 1)
+    bedges = [kc * i / 16 for i in range(17)]
+    pws = torch.empty(g.power_workspace_size(plan, 32), dtype=torch.uint8, device="cuda")
+    bws = torch.empty(g.bispectrum_workspace_size(plan, 16), dtype=torch.uint8, device="cuda")
+    pout = torch.empty(B, 6, 32, dtype=torch.float64, device="cuda")
+    nk = torch.empty(32, dtype=torch.int64, device="cuda")
+    bout = torch.empty(B, 2, 16, dtype=torch.float64, device="cuda")
+
+    def delta(b, n):
+        return d1[b] if n == 1 else spectra[b, n - 2, 0]
+
+    def estimators():
+        for b in range(B):
+            for t, (i, j) in enumerate([(1, 1), (1, 3), (2, 2), (1, 5), (2, 4), (3, 3)]):
+                g.power(plan, delta(b, i), delta(b, j), pedges, ws=pws, out=pout[b, t], nk=nk)
+            E, nt = g.bispectrum(plan, d1[b], spectra[b, 0, 0], bedges, ws=bws)
+            bout[b, 0].copy_(E)
+            bout[b, 1].copy_(nt)
+
+    def step():
+        g.make_linear_field(plan, seeds, out=d1)
+        g.run_orders(plan, d1, spectra=spectra, ws=ws)
+        estimators()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev) if rank == 0 else None
+    g.profile_begin()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = g.profile_end()
+    clk = clocks.stop() if clocks else None
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the public API: delta_1(k) from pinned host memory in,
+    # binned statistics out, every step
+    host_d1 = torch.empty_like(d1, device="cpu").pin_memory()
+    host_d1.copy_(d1.cpu())
+    host_out = torch.empty(B * 6 * 32 + B * 2 * 16, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        d1.copy_(host_d1, non_blocking=True)
+        g.run_orders(plan, d1, spectra=spectra, ws=ws)
+        estimators()
+        host_out[: B * 192].copy_(pout.view(-1), non_blocking=True)
+        host_out[B * 192:].copy_(bout.view(-1), non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    work = world * B * N ** 3 * N_MAX / 1e6
+    value = work / (ms / 1e3)
+    # dominant kernel by summed device time
+    kname, (nl, kms, kbytes) = max(prof.items(), key=lambda kv: kv[1][1])
+    peak, src = peaks()
+    achieved = kbytes / (kms / 1e3) / 1e9
+    rec_kinds = ("ic", "derive_x_inv", "derive_x_fwd_inv", "y_inv", "y_fwd", "x_fwd", "z_c2r", "z_r2c", "product")
+    breakdown = {k: {"launches": v[0], "ms_per_step": round(v[1] / args.steps, 3),
+                     "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    cpu_value, el, reps, cb = oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"gridspt-{N}^3-L{L:g}-nmax{N_MAX}", "grid": N, "box_mpc_h": L, "n_max": N_MAX,
+                   "realisations_per_gpu": B, "estimators": "6 P-terms x 32 log bins + B_tree x 16 shells",
+                   "l2": "inputs larger than L2 (512 MiB fields), no flush", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": NCU_TRAFFIC.get(kname)},
+        "recursion_ms_per_realisation": round(sum(prof[k][1] for k in rec_kinds if k in prof) / args.steps / B, 3),
+        "kernels": breakdown,
+        "clocks": clk,
+        "e2e": {"value": work / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(d1.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
+                "ms_per_step": e2e_ms, "path": "delta_1(k) from pinned host -> run_orders -> estimators -> host"},
+        "cpu_baseline": cb,
+    }
+    # kernels launched per timed region: recorded launches plus the final-reduction kernels
+    # of the estimators (one per power call and per bispectrum shell)
+    extra = args.steps * B * (6 + 16)
+    line["gpu_launches"] = int(sum(v[0] for v in prof.values())) + extra
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--n", type=int, default=N_GRID)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

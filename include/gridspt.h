@@ -1,0 +1,189 @@
+/*
+ * gridspt.h -- C ABI of the GB300 GridSPT library (libgridspt.so).
+ *
+ * GridSPT (Taruya, Nishimichi & Jeong, arXiv:1807.04215) generates standard
+ * perturbation theory density and velocity-divergence fields order by order on
+ * a periodic grid: a Gaussian linear field delta_1 = theta_1 (Eq.
+ * recursion_n=1), then for n = 2..n_max the real-space recursion of Eq.
+ * recursion_formula (Sec. II.B), with spectral derivatives and inverse
+ * Laplacians taken in Fourier space and products in real space, following the
+ * recipe of Sec. II.C. Power spectra (Eqs. pk_lin, pk_1loop, pk_2loop) and the
+ * equilateral bispectrum (Eq. bk_tree) are measured from the spectra.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid: N points per side, N even, N = 2^a or 3 * 2^a, 8 <= N <= 1024; box
+ *   side L (Mpc/h). Signed wavevector index s, k = (2 pi / L) s.
+ * - Transform pair (Sec. II.C): a(x) = sum_k a(k) e^{i k.x},
+ *   a(k) = N^-3 sum_x a(x) e^{-i k.x}.
+ * - Real field: float[N][N][N], z fastest (x_j = j L / N).
+ * - Half spectrum: float2[N][N][N/2] = (re, im), index [kx][ky][kz] with
+ *   kx, ky in FFT order (0..N/2-1, then -N/2..-1) and kz = 0..N/2-1. Modes
+ *   with a component at the Nyquist index -N/2 are zero in every spectrum, so
+ *   the kz = N/2 plane is omitted; a half spectrum has the same byte size as a
+ *   real field (4 N^3 bytes). Modes with kz < 0 follow from a(-k) = conj a(k).
+ * - Every data pointer is a DEVICE pointer to caller-owned memory, aligned to
+ *   16 bytes. The library never allocates, frees or retains caller memory.
+ *   A plan owns a few KB of device tables (allocated in gridspt_plan_create on
+ *   the current device, freed in gridspt_plan_destroy) and nothing else.
+ * - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). All
+ *   compute entry points only enqueue work on `stream` and do not synchronise;
+ *   results are valid once the stream has reached them.
+ * - Errors: arguments are validated before any launch; on failure nothing is
+ *   enqueued and a status != GRIDSPT_OK is returned, with a message available
+ *   from gridspt_last_error() (thread-local). Launch failures return
+ *   GRIDSPT_E_CUDA. No C++ exception crosses the ABI.
+ */
+#ifndef GRIDSPT_H
+#define GRIDSPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRIDSPT_OK = 0,
+    GRIDSPT_E_INVALID = 1,     /* bad argument, size, alignment or workspace */
+    GRIDSPT_E_UNSUPPORTED = 2, /* valid request outside what this build supports */
+    GRIDSPT_E_NOMEM = 3,       /* plan tables could not be allocated */
+    GRIDSPT_E_CUDA = 4,        /* a CUDA runtime call or launch failed */
+    GRIDSPT_E_TIMEOUT = 5,     /* reserved: a bounded device-side wait gave up */
+    GRIDSPT_E_NUMERIC = 6      /* reserved: non-finite result detected */
+} gridspt_status;
+
+typedef struct gridspt_plan_s* gridspt_plan;
+typedef void* gridspt_stream; /* cudaStream_t */
+
+/* Problem description (Sec. II.C: box, grid, highest order, sharp-k cuts). */
+typedef struct {
+    int32_t n;        /* grid points per side */
+    int32_t n_max;    /* highest perturbative order, 1..8 */
+    int32_t batch;    /* realisations per call of make_linear_field / run_orders */
+    int32_t reserved; /* must be 0 */
+    double box;       /* L in Mpc/h, > 0 */
+    double kcut_lin;  /* sharp-k cut on delta_1 in h/Mpc (|k| <= kcut kept);
+                         <= 0 selects 2 k_Ny / (n_max + 1), k_Ny = pi N / L */
+    double kcut_nl;   /* sharp-k cut applied to delta_n, theta_n for n >= 2;
+                         <= 0 means none (only the Nyquist modes are zeroed) */
+} gridspt_desc;
+
+/* Linear spectrum parameters: P(k) = A k^{n_s} T_BBKS(k / Gamma)^2, A fixed by
+ * sigma_8 (top-hat radius 8 Mpc/h); gamma <= 0 selects Gamma = omega_m * h. */
+typedef struct {
+    double omega_m, h, n_s, sigma8, gamma;
+} gridspt_cosmo;
+
+/* Create a plan for `desc` on the current CUDA device (host call; allocates
+ * and uploads the FP32 twiddle table, computed in FP64 on the host).
+ * Returns GRIDSPT_E_INVALID for an unsupported N, n_max, box or batch. */
+gridspt_status gridspt_plan_create(const gridspt_desc* desc, gridspt_plan* out);
+
+/* Release the plan's device tables. Safe on NULL. Synchronises the device. */
+gridspt_status gridspt_plan_destroy(gridspt_plan plan);
+
+/* Bytes of caller workspace gridspt_run_orders needs: the real-space derived
+ * fields of orders 1..n_max-1 (13 for order 1, 17 for each later order, Sec.
+ * II.C steps (2) and (5)), 4 N^3 bytes each. Independent of batch. */
+gridspt_status gridspt_workspace_size(gridspt_plan plan, size_t* bytes);
+
+/* Normalisation A of the linear spectrum (host only, FP64 Simpson in ln k). */
+gridspt_status gridspt_linear_amplitude(const gridspt_cosmo* cosmo, double* amplitude);
+
+/* Sec. II.C step (1): Gaussian delta_1(k) for each realisation b < batch.
+ *   seeds:    HOST uint64[batch], one Philox4x32-10 key per realisation.
+ *   delta1_k: device half spectra float2[batch][N][N][N/2] (written).
+ * Each mode pair {s, -s} draws two uniforms from Philox4x32-10 (Salmon et al.
+ * SC'11) with key = seed and counter = (packed s lo, packed s hi, 0, 0), where
+ * the canonical member c of the pair (c_z > 0, or c_z = 0 and c_y > 0, or
+ * c_z = c_y = 0 and c_x > 0) is packed as three 21-bit two's-complement
+ * fields; u = (r + 1/2) 2^-32, g1 + i g2 = sqrt(-2 ln u1) e^{2 pi i u2},
+ * delta(c) = sqrt(P(|k|) / L^3) (g1 + i g2) / sqrt(2), delta(-c) = conj.
+ * Zero: k = 0, Nyquist modes and |s|^2 > (kcut_lin / k_F)^2. FP64 arithmetic,
+ * stored as FP32. */
+gridspt_status gridspt_make_linear_field(gridspt_plan plan, const gridspt_cosmo* cosmo,
+                                         const uint64_t* seeds, void* delta1_k,
+                                         gridspt_stream stream);
+
+/* Sec. II.C steps (2)-(6) repeated to order n_max (Eq. recursion_formula):
+ *   delta1_k: device float2[batch][N][N][N/2] (read only).
+ *   spectra:  device float2[batch][n_max-1][2][N][N][N/2]; slot [b][n-2][0] is
+ *             delta_n(k), [b][n-2][1] is theta_n(k), n = 2..n_max (written for
+ *             n >= start_order, read for 2 <= n < start_order).
+ *   start_order: 2 for a full run; 3..n_max resumes from stored lower orders
+ *             (Sec. II.C: only delta_m, theta_m are needed to continue).
+ *   ws, ws_bytes: device scratch of at least gridspt_workspace_size bytes.
+ * Realisations run one after another on `stream` and reuse ws. */
+gridspt_status gridspt_run_orders(gridspt_plan plan, const void* delta1_k, int32_t start_order,
+                                  void* spectra, void* ws, size_t ws_bytes,
+                                  gridspt_stream stream);
+
+/* Unnormalised backward transform (Sec. II.C pair) of `count` half spectra
+ * into real fields: out_x[f](x) = sum_k in_k[f](k) e^{i k.x}. in_k and out_x
+ * may be the same buffer (in place); otherwise in_k is left unchanged. */
+gridspt_status gridspt_c2r(gridspt_plan plan, const void* in_k, float* out_x, int32_t count,
+                           gridspt_stream stream);
+
+/* Forward transform of `count` real fields: out_k = N^-3 sum_x in_x e^{-i k.x},
+ * Nyquist modes zeroed. in_x and out_k may be the same buffer. */
+gridspt_status gridspt_r2c(gridspt_plan plan, const float* in_x, void* out_k, int32_t count,
+                           gridspt_stream stream);
+
+/* Shell power estimator (Sec. III.B.1, Eqs. pk_lin/pk_1loop/pk_2loop):
+ *   p_out[i] = L^3 / N_i * sum_{k in bin i} Re[a(k) b*(k)]  over every mode of
+ *   the full grid with k = k_F sqrt(|s|^2) != 0 and edges[i] <= k < edges[i+1].
+ *   a_k, b_k: device half spectra (one realisation each; b_k may equal a_k).
+ *   edges:    HOST double[nbins+1], increasing, edges[nbins] <= k_Ny.
+ *   p_out:    device double[nbins]; nk_out: device int64[nbins] (may be NULL).
+ *   1 <= nbins <= 64. Products in FP32, shell sums in FP64, reduced in a
+ *   fixed order (bitwise repeatable). Cross terms of the paper carry a factor
+ *   2: P_13 = 2 * gridspt_power(delta_1, delta_3). ws: device scratch of
+ *   gridspt_power_workspace_size bytes (per-block partial sums). */
+gridspt_status gridspt_power_workspace_size(gridspt_plan plan, int32_t nbins, size_t* bytes);
+gridspt_status gridspt_power(gridspt_plan plan, const void* a_k, const void* b_k, int32_t nbins,
+                             const double* edges, double* p_out, int64_t* nk_out, void* ws,
+                             size_t ws_bytes, gridspt_stream stream);
+
+/* Equilateral FFT shell bispectrum (Sec. III.B.1, Eq. bk_tree, measured with
+ * an FFT shell estimator): for shell i,
+ *   e_out[i]    = L^6 sum_x I_i[a](x)^2 I_i[b](x) / sum_x J_i(x)^3,
+ *   ntri_out[i] = sum_x J_i(x)^3 / N^3  (closed ordered triangles),
+ * with I_i[f](x) = sum_{k in shell i} f(k) e^{i k.x}, J_i = I_i[1]. The
+ * tree-level bispectrum is B_tree = 3 e_out for a = delta_1, b = delta_2.
+ *   edges: HOST double[nbins+1] with edges[nbins] <= 2 k_Ny / 3 (no wrap);
+ *   e_out, ntri_out: device double[nbins]; 1 <= nbins <= 64. FP32 fields,
+ *   FP64 sums. ws: gridspt_bispectrum_workspace_size bytes of device scratch. */
+gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan plan, int32_t nbins, size_t* bytes);
+gridspt_status gridspt_bispectrum(gridspt_plan plan, const void* a_k, const void* b_k,
+                                  int32_t nbins, const double* edges, double* e_out,
+                                  double* ntri_out, void* ws, size_t ws_bytes,
+                                  gridspt_stream stream);
+
+/* Launch profiling (tracing aid, not part of the paper's method). Between
+ * gridspt_profile_begin and gridspt_profile_end every kernel the library
+ * launches is bracketed by two CUDA events recorded on its launch stream, and
+ * the algorithmic bytes of the launch (each input field read once, each output
+ * written once) are noted. gridspt_profile_end waits for the recorded events
+ * and returns, per kernel kind, the number of launches, the summed event time
+ * in ms and the summed algorithmic bytes (up to `capacity` entries, `*count`
+ * set to the number written). Host calls; not for use inside stream capture.
+ * Process-wide; at most 65536 launches are recorded per session. */
+typedef struct {
+    char name[24];
+    int32_t launches;
+    int32_t reserved;
+    double ms;
+    double bytes;
+} gridspt_kernel_stat;
+gridspt_status gridspt_profile_begin(void);
+gridspt_status gridspt_profile_end(gridspt_kernel_stat* stats, int32_t capacity, int32_t* count);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* gridspt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIDSPT_H */

@@ -1,0 +1,585 @@
+// Host runtime behind include/gridspt.h: argument validation, plan tables,
+// the order-by-order schedule of the Sec. II.C recipe, and the estimator
+// drivers. Every step of the path runs in the CUDA kernels; this file only
+// validates, computes host scalars (FP64 spectrum normalisation, integer bin
+// thresholds) and enqueues launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gridspt.h"
+#include "gridspt_internal.h"
+
+using namespace gridspt;
+
+struct gridspt_plan_s {
+    gridspt_desc d;
+    Geo geo;
+    float2* tw = nullptr;   // device, N entries
+    long long s2_lin;       // keep 0 < |s|^2 <= s2_lin in delta_1
+    long long s2_nl;        // < 0: no cut on higher orders
+    int device = 0;
+    long long pb_top = -1;  // cache of the last power-launch byte count (profiling only)
+    double pb_modes = 0.0;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+gridspt_status fail(gridspt_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+gridspt_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(GRIDSPT_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// ------------------------------------------------------------- profiling
+enum ProfKind {
+    PK_IC, PK_DERIVE_INV, PK_DERIVE_FWD, PK_Y_INV, PK_Y_FWD, PK_X_FWD, PK_ZC2R, PK_ZR2C,
+    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_COUNT
+};
+const char* const kProfNames[PK_COUNT] = {
+    "ic", "derive_x_inv", "derive_x_fwd_inv", "y_inv", "y_fwd", "x_fwd", "z_c2r", "z_r2c",
+    "product", "power", "bispec_reduce"};
+constexpr size_t kMaxProfRecs = 65536;
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+};
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+};
+Profiler g_prof;
+
+cudaEvent_t prof_event() {
+    if (!g_prof.pool.empty()) {
+        cudaEvent_t e = g_prof.pool.back();
+        g_prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch through `f`, bracketed by events on `s` while profiling is on.
+template <class F>
+cudaError_t prof_launch(int kind, double bytes, cudaStream_t s, F&& f) {
+    std::unique_lock<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on || g_prof.recs.size() >= kMaxProfRecs) {
+        lk.unlock();
+        return f();
+    }
+    cudaEvent_t a = prof_event(), b = prof_event();
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, s);
+    if (e != cudaSuccess) return e;
+    e = f();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(b, s);
+    if (e != cudaSuccess) return e;
+    g_prof.recs.push_back({kind, a, b, bytes});
+    return cudaSuccess;
+}
+
+#define CKP(kind, bytes, s, call, where)                                              \
+    do {                                                                              \
+        cudaError_t e_ = prof_launch((kind), (bytes), (s), [&]() { return (call); }); \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);                           \
+    } while (0)
+
+long long field_floats(const gridspt_plan_s* p) { return (long long)p->geo.N * p->geo.N * p->geo.N; }
+long long field_c(const gridspt_plan_s* p) { return (long long)p->geo.N * p->geo.N * p->geo.M; }
+
+int derived_count(int m) { return m == 1 ? 13 : 17; }
+int order_base(int m) { return m == 1 ? 0 : 13 + 17 * (m - 2); }
+int total_derived(int n_max) { return n_max >= 2 ? order_base(n_max) : 0; }
+
+// s2 threshold: smallest integer t >= 0 with kF * sqrt(t) >= e (FP64), so that
+// "t <= |s|^2" is exactly the FP64 test "e <= kF sqrt(|s|^2)".
+long long s2_threshold(double e, double kF) {
+    if (!(e > 0.0)) return 0;
+    double r = e / kF;
+    long long t = (long long)std::floor(r * r);
+    if (t < 0) t = 0;
+    while (t > 0 && kF * std::sqrt((double)(t - 1)) >= e) --t;
+    while (kF * std::sqrt((double)t) < e) ++t;
+    return t;
+}
+
+// ---------------------------------------------------------------- spectrum
+double bbks(double q) {
+    if (q <= 0.0) return 1.0;
+    const double poly = 1.0 + 3.89 * q + std::pow(16.1 * q, 2) + std::pow(5.46 * q, 3) + std::pow(6.71 * q, 4);
+    return std::log1p(2.34 * q) / (2.34 * q) * std::pow(poly, -0.25);
+}
+double gamma_of(const gridspt_cosmo* c) { return c->gamma > 0 ? c->gamma : c->omega_m * c->h; }
+double tophat(double x) {
+    if (std::fabs(x) < 1e-3) return 1.0 - x * x / 10.0 + x * x * x * x / 280.0;
+    return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x);
+}
+// sigma_8^2 for A = 1: (1/2pi^2) int k^3 k^ns T^2 W(8k)^2 dlnk, Simpson, 65536 intervals on [1e-5, 1e3].
+double sigma8_sq_unit(const gridspt_cosmo* c) {
+    const int n = 1 << 16;
+    const double lo = std::log(1e-5), hi = std::log(1e3), h = (hi - lo) / n, G = gamma_of(c);
+    double s = 0.0;
+    for (int i = 0; i <= n; ++i) {
+        const double k = std::exp(lo + h * i);
+        const double t = bbks(k / G), w = tophat(8.0 * k);
+        const double f = k * k * k * std::pow(k, c->n_s) * t * t * w * w;
+        s += f * (i == 0 || i == n ? 1.0 : (i % 2 ? 4.0 : 2.0));
+    }
+    return h / 3.0 * s / (2.0 * M_PI * M_PI);
+}
+
+gridspt_status check_plan(gridspt_plan p) {
+    if (!p) return fail(GRIDSPT_E_INVALID, "plan is NULL");
+    return GRIDSPT_OK;
+}
+
+gridspt_status set_device(const gridspt_plan_s* p) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != p->device) return fail(GRIDSPT_E_INVALID, "plan was created on device %d, current is %d", p->device, cur);
+    return GRIDSPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gridspt_last_error(void) { return g_err; }
+
+gridspt_status gridspt_profile_begin(void) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto& r : g_prof.recs) {
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.recs.clear();
+    g_prof.on = true;
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_profile_end(gridspt_kernel_stat* stats, int32_t capacity, int32_t* count) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = false;
+    double ms[PK_COUNT] = {0}, bytes[PK_COUNT] = {0};
+    int launches[PK_COUNT] = {0};
+    gridspt_status st = GRIDSPT_OK;
+    for (auto& r : g_prof.recs) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && st == GRIDSPT_OK) st = cuda_fail(e, "profile event");
+        ms[r.kind] += t;
+        bytes[r.kind] += r.bytes;
+        launches[r.kind] += 1;
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.recs.clear();
+    int n = 0;
+    for (int k = 0; k < PK_COUNT; ++k) {
+        if (!launches[k]) continue;
+        if (stats && n < capacity) {
+            std::memset(&stats[n], 0, sizeof(stats[n]));
+            std::snprintf(stats[n].name, sizeof(stats[n].name), "%s", kProfNames[k]);
+            stats[n].launches = launches[k];
+            stats[n].ms = ms[k];
+            stats[n].bytes = bytes[k];
+        }
+        ++n;
+    }
+    if (count) *count = std::min(n, capacity);
+    return st;
+}
+
+gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
+    g_err[0] = 0;
+    if (!d || !out) return fail(GRIDSPT_E_INVALID, "desc/out is NULL");
+    *out = nullptr;
+    if (!supported_n(d->n)) return fail(GRIDSPT_E_INVALID, "n=%d: need even N = 2^a or 3*2^a, 8 <= N <= 1024", d->n);
+    if (d->n_max < 1 || d->n_max > kMaxOrder) return fail(GRIDSPT_E_INVALID, "n_max=%d outside [1, %d]", d->n_max, kMaxOrder);
+    if (d->batch < 1) return fail(GRIDSPT_E_INVALID, "batch=%d < 1", d->batch);
+    if (!(d->box > 0.0) || !std::isfinite(d->box)) return fail(GRIDSPT_E_INVALID, "box must be > 0");
+    if (d->reserved != 0) return fail(GRIDSPT_E_INVALID, "reserved field must be 0");
+    gridspt_plan_s* p = new (std::nothrow) gridspt_plan_s();
+    if (!p) return fail(GRIDSPT_E_NOMEM, "host allocation failed");
+    p->d = *d;
+    const int N = d->n;
+    p->geo.N = N;
+    p->geo.M = N / 2;
+    p->geo.kF = 2.0 * M_PI / d->box;
+    const double r = d->kcut_lin > 0 ? d->kcut_lin * d->box / (2.0 * M_PI) : (double)N / (d->n_max + 1);
+    p->s2_lin = (long long)std::floor(r * r);
+    if (d->kcut_nl > 0) {
+        const double rn = d->kcut_nl * d->box / (2.0 * M_PI);
+        p->s2_nl = (long long)std::floor(rn * rn);
+    } else {
+        p->s2_nl = -1;
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    std::vector<float2> tw(N);
+    for (int j = 0; j < N; ++j) {
+        const double a = 2.0 * M_PI * (double)j / (double)N;
+        tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    e = cudaMalloc(&p->tw, sizeof(float2) * N);
+    if (e != cudaSuccess) { delete p; return fail(GRIDSPT_E_NOMEM, "twiddle table: %s", cudaGetErrorString(e)); }
+    e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(p->tw); delete p; return cuda_fail(e, "twiddle upload"); }
+    p->geo.tw = p->tw;
+    *out = p;
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_plan_destroy(gridspt_plan p) {
+    if (!p) return GRIDSPT_OK;
+    cudaError_t e = cudaSuccess;
+    if (p->tw) {
+        e = cudaDeviceSynchronize();
+        cudaError_t e2 = cudaFree(p->tw);
+        if (e == cudaSuccess) e = e2;
+    }
+    delete p;
+    if (e != cudaSuccess) return cuda_fail(e, "plan_destroy");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_workspace_size(gridspt_plan p, size_t* bytes) {
+    if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
+    *bytes = (size_t)total_derived(p->d.n_max) * (size_t)field_floats(p) * sizeof(float);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_linear_amplitude(const gridspt_cosmo* c, double* A) {
+    if (!c || !A) return fail(GRIDSPT_E_INVALID, "cosmo/A is NULL");
+    if (!(c->sigma8 > 0) || !(gamma_of(c) > 0)) return fail(GRIDSPT_E_INVALID, "sigma8 and Gamma must be > 0");
+    *A = c->sigma8 * c->sigma8 / sigma8_sq_unit(c);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_make_linear_field(gridspt_plan p, const gridspt_cosmo* c, const uint64_t* seeds,
+                                         void* delta1_k, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!c || !seeds || !delta1_k) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!aligned16(delta1_k)) return fail(GRIDSPT_E_INVALID, "delta1_k not 16-byte aligned");
+    if (gridspt_status st = set_device(p)) return st;
+    double A = 0.0;
+    if (gridspt_status st = gridspt_linear_amplitude(c, &A)) return st;
+    IcArgs a{};
+    a.amp = A;
+    a.n_s = c->n_s;
+    a.gamma = gamma_of(c);
+    a.inv_vol = 1.0 / (p->d.box * p->d.box * p->d.box);
+    a.s2_cut = p->s2_lin;
+    for (int b = 0; b < p->d.batch; ++b) {
+        a.out = static_cast<float2*>(delta1_k) + (long long)b * field_c(p);
+        a.seed = seeds[b];
+        CKP(PK_IC, 4.0 * (double)field_floats(p), (cudaStream_t)stream, launch_ic(p->geo, a, (cudaStream_t)stream),
+            "ic launch");
+    }
+    return GRIDSPT_OK;
+}
+
+namespace {
+
+// Derived fields of order m from its spectra (delta_m, theta_m), written to
+// ws at the order's slot, through the backward x, y, z passes. With fwd, the
+// spectra buffers hold the y-transformed product output and the x pass first
+// completes the forward transform (writing delta_m(k), theta_m(k) in place).
+gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* tk, float* ws,
+                            bool fwd, cudaStream_t s) {
+    DeriveArgs a{};
+    a.src0 = dk;
+    a.src1 = tk;
+    const long long F = field_c(p);
+    float2* out = reinterpret_cast<float2*>(ws + (long long)order_base(m) * field_floats(p));
+    a.out = out;
+    a.out_stride = F;
+    a.fwd_first = fwd ? 1 : 0;
+    a.s2_nl = p->s2_nl;
+    int k = 0;
+    if (m == 1) {
+        a.codes[k++] = derive_code(DK_ONE, 0, 0, 0);
+        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_IK, c, 0, 0);
+        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_NEG_IK_K2, c, 0, 0);
+    } else {
+        a.codes[k++] = derive_code(DK_ONE, 0, 0, 0);
+        a.codes[k++] = derive_code(DK_ONE, 0, 0, 1);
+        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_IK, c, 0, 0);
+        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_IK, c, 0, 1);
+        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_NEG_IK_K2, c, 0, 1);
+    }
+    const int src_t = m == 1 ? 0 : 1;
+    const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int t = 0; t < 6; ++t) a.codes[k++] = derive_code(DK_KK_K2, pairs[t][0], pairs[t][1], src_t);
+    a.nout = k;
+    const double fb = 4.0 * (double)field_floats(p);  // bytes of one field
+    const int nin = m == 1 ? 1 : 2;
+    CKP(fwd ? PK_DERIVE_FWD : PK_DERIVE_INV, fb * (fwd ? 2 * nin + k : nin + k), s,
+        launch_derive(p->geo, a, s), "derive launch");
+    CKP(PK_Y_INV, 2 * fb * k, s, launch_colpass(p->geo, out, F, k, 1, +1, 0, -1, s), "y pass");
+    CKP(PK_ZC2R, 2 * fb * k, s, launch_zc2r(p->geo, out, out, F, k, s), "z c2r");
+    return GRIDSPT_OK;
+}
+
+}  // namespace
+
+gridspt_status gridspt_run_orders(gridspt_plan p, const void* delta1_k, int32_t start_order, void* spectra,
+                                  void* ws, size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    const int n_max = p->d.n_max;
+    if (!delta1_k || (!spectra && n_max >= 2)) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!aligned16(delta1_k) || !aligned16(spectra) || !aligned16(ws))
+        return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    if (n_max < 2) return GRIDSPT_OK;
+    if (start_order < 2 || start_order > n_max) return fail(GRIDSPT_E_INVALID, "start_order=%d outside [2, %d]", start_order, n_max);
+    size_t need = 0;
+    gridspt_workspace_size(p, &need);
+    if (!ws || ws_bytes < need) return fail(GRIDSPT_E_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (gridspt_status st = set_device(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long F = field_c(p);
+    const double inv_cells = 1.0 / (double)field_floats(p);
+    float* w = static_cast<float*>(ws);
+    for (int b = 0; b < p->d.batch; ++b) {
+        float2* d1 = const_cast<float2*>(static_cast<const float2*>(delta1_k)) + (long long)b * F;
+        auto spec = [&](int n, int which) {
+            return static_cast<float2*>(spectra) + ((long long)(b * (n_max - 1) + (n - 2)) * 2 + which) * F;
+        };
+        // derived fields of the orders below start_order, from stored spectra
+        if (gridspt_status st = derive_order(p, 1, d1, d1, w, false, s)) return st;
+        for (int m = 2; m < start_order; ++m)
+            if (gridspt_status st = derive_order(p, m, spec(m, 0), spec(m, 1), w, false, s)) return st;
+        for (int n = start_order; n <= n_max; ++n) {
+            ProductArgs pa{};
+            pa.ws = w;
+            pa.cells = field_floats(p);
+            for (int m = 1; m <= kMaxOrder; ++m) pa.base[m] = order_base(m);
+            pa.n = n;
+            pa.out_delta = reinterpret_cast<float*>(spec(n, 0));
+            pa.out_theta = reinterpret_cast<float*>(spec(n, 1));
+            const double c = 2.0 / ((2.0 * n + 3.0) * (n - 1.0));
+            pa.cdA = (float)(c * (n + 0.5) * inv_cells);
+            pa.cdB = (float)(c * inv_cells);
+            pa.ctA = (float)(c * 1.5 * inv_cells);
+            pa.ctB = (float)(c * n * inv_cells);
+            const double fb = 4.0 * (double)field_floats(p);
+            CKP(PK_PRODUCT, fb * (order_base(n) + 2), s, launch_product(p->geo, pa, s), "product launch");
+            CKP(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, spec(n, 0), spec(n, 0), F, 2, 1.0f, s), "z r2c");
+            CKP(PK_Y_FWD, 4 * fb, s, launch_colpass(p->geo, spec(n, 0), F, 2, 1, -1, 0, -1, s), "y pass fwd");
+            if (n < n_max) {
+                if (gridspt_status st = derive_order(p, n, spec(n, 0), spec(n, 1), w, true, s)) return st;
+            } else {
+                CKP(PK_X_FWD, 4 * fb, s, launch_colpass(p->geo, spec(n, 0), F, 2, 0, -1, 1, p->s2_nl, s),
+                    "x pass fwd");
+            }
+        }
+    }
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_c2r(gridspt_plan p, const void* in_k, float* out_x, int32_t count, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!in_k || !out_x || count < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or count < 1");
+    if (!aligned16(in_k) || !aligned16(out_x)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    if (gridspt_status st = set_device(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long F = field_c(p);
+    for (int f = 0; f < count; ++f) {
+        DeriveArgs a{};
+        a.src0 = a.src1 = const_cast<float2*>(static_cast<const float2*>(in_k)) + f * F;
+        a.out = reinterpret_cast<float2*>(out_x) + f * F;
+        a.out_stride = F;
+        a.nout = 1;
+        a.codes[0] = derive_code(DK_ONE, 0, 0, 0);
+        a.s2_nl = -1;
+        CK(launch_derive(p->geo, a, s), "x pass");
+    }
+    float2* o = reinterpret_cast<float2*>(out_x);
+    CK(launch_colpass(p->geo, o, F, count, 1, +1, 0, -1, s), "y pass");
+    CK(launch_zc2r(p->geo, o, o, F, count, s), "z c2r");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_r2c(gridspt_plan p, const float* in_x, void* out_k, int32_t count, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!in_x || !out_k || count < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or count < 1");
+    if (!aligned16(in_x) || !aligned16(out_k)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    if (gridspt_status st = set_device(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long F = field_c(p);
+    float2* o = static_cast<float2*>(out_k);
+    const float scale = (float)(1.0 / (double)field_floats(p));
+    CK(launch_zr2c(p->geo, reinterpret_cast<const float2*>(in_x), o, F, count, scale, s), "z r2c");
+    CK(launch_colpass(p->geo, o, F, count, 1, -1, 0, -1, s), "y pass");
+    CK(launch_colpass(p->geo, o, F, count, 0, -1, 1, -1, s), "x pass");
+    return GRIDSPT_OK;
+}
+
+namespace {
+
+// Algorithmic bytes of one power launch: each stored mode below the top edge
+// read once from each input (8 bytes per mode and input).
+double power_bytes(gridspt_plan_s* p, long long top, bool same) {
+    if (!g_prof.on) return 0.0;
+    if (p->pb_top == top) return 8.0 * p->pb_modes * (same ? 1 : 2);
+    const int N = p->geo.N, M = p->geo.M;
+    long long modes = 0;
+    for (int kx = 0; kx < N; ++kx)
+        for (int ky = 0; ky < N; ++ky) {
+            const long long sx = kx < N / 2 ? kx : kx - N, sy = ky < N / 2 ? ky : ky - N;
+            const long long rem = top - sx * sx - sy * sy;
+            if (rem <= 0) continue;
+            long long kz = (long long)std::sqrt((double)rem);
+            while (kz * kz >= rem) --kz;
+            while ((kz + 1) * (kz + 1) < rem) ++kz;
+            modes += std::min<long long>(kz + 1, M);
+        }
+    p->pb_top = top;
+    p->pb_modes = (double)modes;
+    return 8.0 * (double)modes * (same ? 1 : 2);
+}
+
+gridspt_status make_bins(const gridspt_plan_s* p, int nbins, const double* edges, double kmax, BinSpec* bs) {
+    if (nbins < 1 || nbins > kMaxBins) return fail(GRIDSPT_E_INVALID, "nbins=%d outside [1, %d]", nbins, kMaxBins);
+    if (!edges) return fail(GRIDSPT_E_INVALID, "edges is NULL");
+    for (int i = 0; i < nbins; ++i)
+        if (!(edges[i] < edges[i + 1]) || !(edges[i] >= 0.0))
+            return fail(GRIDSPT_E_INVALID, "edges must be non-negative and increasing");
+    bs->nbins = nbins;
+    for (int i = 0; i <= nbins; ++i) bs->thr[i] = (int)s2_threshold(edges[i], p->geo.kF);
+    (void)kmax;
+    return GRIDSPT_OK;
+}
+
+}  // namespace
+
+gridspt_status gridspt_power_workspace_size(gridspt_plan p, int32_t nbins, size_t* bytes) {
+    if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
+    if (nbins < 1 || nbins > kMaxBins) return fail(GRIDSPT_E_INVALID, "nbins=%d outside [1, %d]", nbins, kMaxBins);
+    *bytes = (size_t)power_blocks(p->geo) * 2 * nbins * sizeof(double);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_power(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins, const double* edges,
+                             double* p_out, int64_t* nk_out, void* ws, size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!a_k || !b_k || !p_out) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!aligned16(a_k) || !aligned16(b_k) || !aligned16(ws)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    BinSpec bs{};
+    if (gridspt_status st = make_bins(p, nbins, edges, 0, &bs)) return st;
+    const long long half = p->geo.N / 2;
+    if (bs.thr[nbins] > half * half) return fail(GRIDSPT_E_INVALID, "last edge above the Nyquist wavenumber");
+    size_t need = 0;
+    gridspt_power_workspace_size(p, nbins, &need);
+    if (!ws || ws_bytes < need) return fail(GRIDSPT_E_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (gridspt_status st = set_device(p)) return st;
+    const double vol = p->d.box * p->d.box * p->d.box;
+    CKP(PK_POWER, power_bytes(p, bs.thr[nbins], a_k == b_k), (cudaStream_t)stream,
+        launch_power(p->geo, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k), bs,
+                     static_cast<double*>(ws), p_out, nk_out, vol, (cudaStream_t)stream), "power launch");
+    return GRIDSPT_OK;
+}
+
+namespace {
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}
+
+gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan p, int32_t nbins, size_t* bytes) {
+    if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
+    if (nbins < 1 || nbins > kMaxBins) return fail(GRIDSPT_E_INVALID, "nbins=%d outside [1, %d]", nbins, kMaxBins);
+    *bytes = 3 * align256((size_t)field_floats(p) * sizeof(float)) + align256((size_t)bispec_blocks(p->geo) * 2 * sizeof(double));
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins,
+                                  const double* edges, double* e_out, double* ntri_out, void* ws,
+                                  size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!a_k || !b_k || !e_out || !ntri_out) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!aligned16(a_k) || !aligned16(b_k) || !aligned16(ws)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    BinSpec bs{};
+    if (gridspt_status st = make_bins(p, nbins, edges, 0, &bs)) return st;
+    const long long maxs2 = (long long)bs.thr[nbins] - 1;
+    if (9 * maxs2 >= (long long)p->geo.N * p->geo.N)
+        return fail(GRIDSPT_E_INVALID, "last edge must lie below 2 k_Ny / 3 (shell vectors |s| < N/3)");
+    size_t need = 0;
+    gridspt_bispectrum_workspace_size(p, nbins, &need);
+    if (!ws || ws_bytes < need) return fail(GRIDSPT_E_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (gridspt_status st = set_device(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long F = field_c(p);
+    const size_t fb = align256((size_t)field_floats(p) * sizeof(float));
+    char* base = static_cast<char*>(ws);
+    float2* fields = reinterpret_cast<float2*>(base);
+    double* partial = reinterpret_cast<double*>(base + 3 * fb);
+    const double L = p->d.box;
+    for (int i = 0; i < nbins; ++i) {
+        DeriveArgs a{};
+        a.src0 = const_cast<float2*>(static_cast<const float2*>(a_k));
+        a.src1 = const_cast<float2*>(static_cast<const float2*>(b_k));
+        a.out = fields;
+        a.out_stride = (long long)(fb / sizeof(float2));
+        a.nout = 3;
+        a.codes[0] = derive_code(DK_SHELL, 0, 0, 0);
+        a.codes[1] = derive_code(DK_SHELL, 0, 0, 1);
+        a.codes[2] = derive_code(DK_SHELL, 0, 0, 2);
+        a.s2_nl = -1;
+        a.shell_lo = bs.thr[i];
+        a.shell_hi = bs.thr[i + 1];
+        if (a.src1 == a.src0) {
+            // the kernel treats equal inputs as one; keep the second output explicit
+            a.codes[1] = derive_code(DK_SHELL, 0, 0, 0);
+        }
+        const double fbytes = 4.0 * (double)field_floats(p);
+        CKP(PK_DERIVE_INV, fbytes * (2 + 3), s, launch_derive(p->geo, a, s), "bispectrum shell x pass");
+        CKP(PK_Y_INV, 2 * fbytes * 3, s, launch_colpass(p->geo, fields, a.out_stride, 3, 1, +1, 0, -1, s),
+            "bispectrum y pass");
+        CKP(PK_ZC2R, 2 * fbytes * 3, s, launch_zc2r(p->geo, fields, fields, a.out_stride, 3, s), "bispectrum z pass");
+        const float* f0 = reinterpret_cast<const float*>(base);
+        CKP(PK_BISPEC, 3 * fbytes, s,
+            launch_bispec_reduce(p->geo, f0, reinterpret_cast<const float*>(base + fb),
+                                 reinterpret_cast<const float*>(base + 2 * fb), partial, e_out + i, ntri_out + i,
+                                 L * L * L * L * L * L, s),
+            "bispectrum reduce");
+    }
+    return GRIDSPT_OK;
+}
+
+}  // extern "C"

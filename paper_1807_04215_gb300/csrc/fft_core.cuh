@@ -1,0 +1,174 @@
+// Register-resident Stockham FFT used by every transform pass of the library.
+//
+// A batch of independent length-L transforms ("columns") is processed by one
+// thread block. Thread p (0 <= p < P = L / E) of a column holds the E elements
+// n = p + P * i (i = 0..E-1) in registers. Each radix-R stage does E / R
+// butterflies per thread entirely in registers; between stages the outputs go
+// through a shared-memory exchange buffer (Stockham autosort ordering), and
+// after the last stage the thread again holds n = p + P * i in natural order,
+// so a forward transform can feed an inverse transform without touching
+// shared memory (used by the fused spectral-derivative pass).
+//
+// Sign convention: DIR = +1 computes y[n] = sum_t x[t] e^{+2 pi i n t / L}
+// (the backward/synthesis sum of the paper's transform pair, Sec. II.C),
+// DIR = -1 the analysis sum with e^{-...}; neither is normalised.
+//
+// Twiddle factors are read from a table of the N-th roots of unity
+// e^{+2 pi i j / N} (FP64 on the host, rounded to FP32) held in shared memory;
+// a length-L transform (L divides N) uses every (N / L)-th entry.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gridspt {
+
+// ----------------------------------------------------------- complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by DIR * i
+template <int DIR>
+__device__ __forceinline__ float2 cmul_i(float2 a) {
+    return DIR > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ------------------------------------------------------- radix schedule (L)
+// Power-of-two lengths use E = 8 elements per thread: radix-8 stages and one
+// final radix-2 or radix-4 stage. Lengths 3 * 2^a use E = 12 (E = 6 for L = 6):
+// one radix-3 stage, then radix-4 stages and possibly one radix-2 stage.
+__host__ __device__ constexpr bool fft_has3(int L) { return L % 3 == 0; }
+__host__ __device__ constexpr int fft_pow2_part(int L) { return fft_has3(L) ? L / 3 : L; }
+__host__ __device__ constexpr int fft_base(int L) { return fft_has3(L) ? 4 : 8; }
+__host__ __device__ constexpr int fft_fullb(int m, int b) { return m >= b ? 1 + fft_fullb(m / b, b) : 0; }
+__host__ __device__ constexpr int fft_remb(int m, int b) { return m >= b ? fft_remb(m / b, b) : m; }
+__host__ __device__ constexpr int fft_nstages(int L) {
+    return (fft_has3(L) ? 1 : 0) + fft_fullb(fft_pow2_part(L), fft_base(L)) +
+           (fft_remb(fft_pow2_part(L), fft_base(L)) > 1 ? 1 : 0);
+}
+__host__ __device__ constexpr int fft_radix_p2(int m, int s, int b) {
+    return s < fft_fullb(m, b) ? b : fft_remb(m, b);
+}
+__host__ __device__ constexpr int fft_radix(int L, int s) {
+    return fft_has3(L) ? (s == 0 ? 3 : fft_radix_p2(fft_pow2_part(L), s - 1, 4))
+                       : fft_radix_p2(L, s, 8);
+}
+__host__ __device__ constexpr int fft_ls(int L, int s) {  // product of radices before stage s
+    return s == 0 ? 1 : fft_ls(L, s - 1) * fft_radix(L, s - 1);
+}
+__host__ __device__ constexpr int fft_elems(int L) {
+    return fft_has3(L) ? (L >= 12 ? 12 : L) : (L >= 8 ? 8 : L);
+}
+
+// ------------------------------------------------------------ small DFTs
+template <int R, int DIR>
+__device__ __forceinline__ void dft_small(float2* v) {
+    if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        const float h = 0.86602540378443864676f;  // sqrt(3) / 2
+        float2 s = cadd(v[1], v[2]);
+        float2 d = csub(v[1], v[2]);
+        float2 m = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
+        float2 r = cscale(cmul_i<DIR>(d), h);
+        v[0] = cadd(v[0], s);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    } else if constexpr (R == 4) {
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = cmul_i<DIR>(csub(v[1], v[3]));
+        v[0] = cadd(a0, b0);
+        v[2] = csub(a0, b0);
+        v[1] = cadd(a1, b1);
+        v[3] = csub(a1, b1);
+    } else if constexpr (R == 8) {
+        const float r2 = 0.70710678118654752440f;  // 1 / sqrt(2)
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        dft_small<4, DIR>(e);
+        dft_small<4, DIR>(o);
+        // o[t] *= w8^t, w8 = (1 + DIR i) / sqrt(2)
+        o[1] = cscale(cadd(o[1], cmul_i<DIR>(o[1])), r2);
+        o[2] = cmul_i<DIR>(o[2]);
+        o[3] = cscale(csub(cmul_i<DIR>(o[3]), o[3]), r2);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            v[t] = cadd(e[t], o[t]);
+            v[t + 4] = csub(e[t], o[t]);
+        }
+    }
+}
+
+// ------------------------------------------------------------- one stage
+// Shared-memory exchange buffer of one column: element n at col[n * SN].
+template <int L, int S, int DIR, int N>
+__device__ __forceinline__ void fft_stage(float2 (&x)[fft_elems(L)], int p, float2* col, int SN,
+                                          const float2* __restrict__ tw) {
+    constexpr int E = fft_elems(L);
+    constexpr int P = L / E;
+    constexpr int R = fft_radix(L, S);
+    constexpr int Ls = fft_ls(L, S);
+    constexpr int Q = E / R;              // butterflies per thread
+    constexpr int NS = fft_nstages(L);
+    constexpr bool last = (S == NS - 1);
+    constexpr int TWS = N / (Ls * R);     // table stride for angle t * k / (Ls * R)
+    float2 y[E];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 v[R];
+        const int b = p + q * P;          // butterfly index
+        const int k = (Ls == 1) ? 0 : (b % Ls);
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = x[q + t * Q];
+        if constexpr (Ls > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w = tw[t * k * TWS];  // t * k < Ls * R, so the index is < N
+                if (DIR < 0) w.y = -w.y;
+                v[t] = cmul(v[t], w);
+            }
+        }
+        dft_small<R, DIR>(v);
+        if constexpr (last) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) y[q + t * Q] = v[t];
+        } else {
+            const int base = (b / Ls) * Ls * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) col[(base + t * Ls) * SN] = v[t];
+        }
+    }
+    if constexpr (last) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = y[i];
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = col[(p + P * i) * SN];
+        __syncthreads();
+    }
+}
+
+template <int L, int S, int DIR, int N>
+__device__ __forceinline__ void fft_stages(float2 (&x)[fft_elems(L)], int p, float2* col, int SN,
+                                           const float2* __restrict__ tw) {
+    if constexpr (S < fft_nstages(L)) {
+        fft_stage<L, S, DIR, N>(x, p, col, SN, tw);
+        fft_stages<L, S + 1, DIR, N>(x, p, col, SN, tw);
+    }
+}
+
+// Full length-L transform of the column whose exchange buffer is `col`
+// (stride SN float2). Every thread of the block must call it the same number
+// of times (it contains __syncthreads). tw: shared table of N-th roots.
+template <int L, int DIR, int N>
+__device__ __forceinline__ void fft_column(float2 (&x)[fft_elems(L)], int p, float2* col, int SN,
+                                           const float2* __restrict__ tw) {
+    fft_stages<L, 0, DIR, N>(x, p, col, SN, tw);
+}
+
+}  // namespace gridspt

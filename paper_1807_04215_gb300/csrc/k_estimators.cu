@@ -1,0 +1,195 @@
+// Shell estimators (Sec. III.B.1).
+//
+// Power (Eqs. pk_lin, pk_1loop, pk_2loop): P_ab(i) = L^3 / N_i sum_{k in bin i}
+// Re[a(k) b*(k)] over the full grid. The half spectrum stores kz >= 0; modes
+// with kz > 0 stand for themselves and their conjugate partners (weight 2),
+// the kz = 0 plane holds both members of each pair (weight 1). Bins are
+// integer ranges of |s|^2 precomputed on the host from the FP64 edges, so
+// the bin decision equals the FP64 test edges[i] <= k_F sqrt(|s|^2).
+//
+// Determinism: one warp per (kx, ky) row, 32 consecutive kz per step. Along a
+// row the bin index is non-decreasing in kz, so lanes with equal bins are
+// contiguous: a segmented shuffle scan sums each run and its last lane adds
+// the run to the warp's FP64 accumulator (one writer per bin per step). Warps
+// and blocks are then summed in a fixed order: results are bitwise repeatable.
+//
+// Bispectrum (Eq. bk_tree, FFT shell estimator): sums over cells of
+// I_a(x)^2 I_b(x) and J(x)^3 in FP64 (four-cell FP32 partial products),
+// fixed-order block and grid reductions.
+#include "gridspt_internal.h"
+
+namespace gridspt {
+
+constexpr int kPowWarps = 8;
+
+int power_blocks(const Geo& g) {
+    const long long rows = (long long)g.N * g.N;
+    long long b = (rows + kPowWarps - 1) / kPowWarps;
+    return (int)(b < 1216 ? b : 1216);
+}
+
+__global__ void __launch_bounds__(kPowWarps * 32)
+k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins, int N, int M,
+        double* __restrict__ partial) {
+    __shared__ double acc[kPowWarps][2 * kMaxBins];
+    __shared__ int thr[kMaxBins + 1];
+    const int nb = bins.nbins;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kPowWarps * 2 * kMaxBins; i += blockDim.x) (&acc[0][0])[i] = 0.0;
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x) thr[i] = bins.thr[i];
+    __syncthreads();
+    const int top = thr[nb];
+    const long long rows = (long long)N * N;
+    for (long long row = (long long)blockIdx.x * kPowWarps + w; row < rows;
+         row += (long long)gridDim.x * kPowWarps) {
+        const int kx = (int)(row / N), ky = (int)(row % N);
+        const int sx = kx < N / 2 ? kx : kx - N;
+        const int sy = ky < N / 2 ? ky : ky - N;
+        const int sxy = sx * sx + sy * sy;
+        if (sxy >= top) continue;
+        const float2* ar = a + row * M;
+        const float2* br = b + row * M;
+        for (int kz0 = 0; kz0 < M; kz0 += 32) {
+            if (sxy + kz0 * kz0 >= top) break;
+            const int kz = kz0 + lane;
+            const int s2 = sxy + kz * kz;
+            int bin;
+            if (kz >= M || s2 >= top) {
+                bin = nb;                       // above every bin
+            } else if (s2 == 0 || s2 < thr[0]) {
+                bin = -1;                       // k = 0 or below the first edge
+            } else {
+                int lo = 0, hi = nb;            // thr[lo] <= s2 < thr[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (thr[mid] <= s2) lo = mid; else hi = mid;
+                }
+                bin = lo;
+            }
+            double v = 0.0, c = 0.0;
+            if (bin >= 0 && bin < nb) {
+                const float2 x = ar[kz], y = br[kz];
+                const float wgt = kz == 0 ? 1.f : 2.f;
+                v = (double)(wgt * fmaf(x.x, y.x, x.y * y.y));
+                c = (double)wgt;
+            }
+            // segmented inclusive scan over runs of equal bin
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const double ov = __shfl_up_sync(0xffffffffu, v, off);
+                const double oc = __shfl_up_sync(0xffffffffu, c, off);
+                const int ob = __shfl_up_sync(0xffffffffu, bin, off);
+                if (lane >= off && ob == bin) {
+                    v += ov;
+                    c += oc;
+                }
+            }
+            const int nxt = __shfl_down_sync(0xffffffffu, bin, 1);
+            const bool tail = (lane == 31) || (nxt != bin);
+            if (tail && bin >= 0 && bin < nb) {
+                acc[w][bin] += v;
+                acc[w][kMaxBins + bin] += c;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        double s = 0.0, c = 0.0;
+        for (int ww = 0; ww < kPowWarps; ++ww) {
+            s += acc[ww][t];
+            c += acc[ww][kMaxBins + t];
+        }
+        partial[(long long)blockIdx.x * 2 * nb + t] = s;
+        partial[(long long)blockIdx.x * 2 * nb + nb + t] = c;
+    }
+}
+
+__global__ void k_power_final(const double* __restrict__ partial, int G, int nb, double vol,
+                              double* __restrict__ p_out, int64_t* __restrict__ nk_out) {
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        double s = 0.0, c = 0.0;
+        for (int g = 0; g < G; ++g) {
+            s += partial[(long long)g * 2 * nb + t];
+            c += partial[(long long)g * 2 * nb + nb + t];
+        }
+        p_out[t] = c > 0.0 ? vol * s / c : 0.0;
+        if (nk_out) nk_out[t] = (int64_t)(c + 0.5);
+    }
+}
+
+cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const BinSpec& bins,
+                         double* partial, double* p_out, int64_t* nk_out, double volume,
+                         cudaStream_t s) {
+    const int G = power_blocks(g);
+    k_power<<<G, kPowWarps * 32, 0, s>>>(a, b, bins, g.N, g.M, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_power_final<<<1, 64, 0, s>>>(partial, G, bins.nbins, volume, p_out, nk_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ bispectrum
+constexpr int kBisThreads = 256;
+
+int bispec_blocks(const Geo& g) {
+    const long long n4 = (long long)g.N * g.N * g.N / 4;
+    long long b = (n4 + kBisThreads - 1) / kBisThreads;
+    return (int)(b < 1216 ? b : 1216);
+}
+
+__global__ void __launch_bounds__(kBisThreads)
+k_bispec(const float4* __restrict__ ia, const float4* __restrict__ ib, const float4* __restrict__ jj,
+         long long n4, double* __restrict__ partial) {
+    __shared__ double r1[kBisThreads], r2[kBisThreads];
+    double s1 = 0.0, s2 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = ia[i], b = ib[i], j = jj[i];
+        s1 += (double)(a.x * a.x * b.x + a.y * a.y * b.y) + (double)(a.z * a.z * b.z + a.w * a.w * b.w);
+        s2 += (double)(j.x * j.x * j.x + j.y * j.y * j.y) + (double)(j.z * j.z * j.z + j.w * j.w * j.w);
+    }
+    r1[threadIdx.x] = s1;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int h = kBisThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            r1[threadIdx.x] += r1[threadIdx.x + h];
+            r2[threadIdx.x] += r2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = r1[0];
+        partial[2 * blockIdx.x + 1] = r2[0];
+    }
+}
+
+__global__ void k_bispec_final(const double* __restrict__ partial, int G, double vol2, double cells,
+                               double* __restrict__ e_out, double* __restrict__ ntri_out) {
+    if (threadIdx.x != 0) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int g = 0; g < G; ++g) {
+        s1 += partial[2 * g];
+        s2 += partial[2 * g + 1];
+    }
+    const double nt = s2 / cells;
+    *ntri_out = nt;
+    *e_out = nt > 0.5 ? vol2 * s1 / s2 : 0.0;
+}
+
+cudaError_t launch_bispec_reduce(const Geo& g, const float* ia, const float* ib, const float* j,
+                                 double* partial, double* e_out, double* ntri_out, double vol2,
+                                 cudaStream_t s) {
+    const int G = bispec_blocks(g);
+    const long long n4 = (long long)g.N * g.N * g.N / 4;
+    k_bispec<<<G, kBisThreads, 0, s>>>(reinterpret_cast<const float4*>(ia),
+                                       reinterpret_cast<const float4*>(ib),
+                                       reinterpret_cast<const float4*>(j), n4, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bispec_final<<<1, 32, 0, s>>>(partial, G, vol2, (double)g.N * g.N * g.N, e_out, ntri_out);
+    return cudaGetLastError();
+}
+
+}  // namespace gridspt

@@ -1,0 +1,202 @@
+"""Python binding of libgridspt.so with the C-ABI's names (include/gridspt.h).
+
+Tensors are torch CUDA tensors used only as device memory: half spectra are
+complex64 [..., N, N, N/2] (interleaved re/im = float2), real fields float32
+[..., N, N, N]. Each function checks shapes, allocates outputs and scratch
+with torch, and passes raw pointers plus the current torch stream to the
+library; every step of the computation runs in the library's CUDA kernels.
+"""
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+DEFAULT_COSMO = dict(omega_m=0.3, h=0.7, n_s=0.96, sigma8=0.8, gamma=0.0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+@dataclass
+class Desc:
+    n: int
+    n_max: int
+    box: float
+    batch: int = 1
+    kcut_lin: float = 0.0
+    kcut_nl: float = 0.0
+
+
+class Plan:
+    """Owns a gridspt_plan (twiddle table on the current device)."""
+
+    def __init__(self, n, n_max, box, batch=1, kcut_lin=0.0, kcut_nl=0.0):
+        self.lib = _lib.load()
+        self.desc = Desc(n, n_max, box, batch, kcut_lin, kcut_nl)
+        d = _lib.GridsptDesc(n, n_max, batch, 0, box, kcut_lin, kcut_nl)
+        h = ctypes.c_void_p()
+        _lib.check("gridspt_plan_create", self.lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.n, self.m, self.n_max, self.batch, self.box = n, n // 2, n_max, batch, box
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.check("gridspt_plan_destroy", self.lib.gridspt_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- shapes
+    def half_shape(self, *lead):
+        return tuple(lead) + (self.n, self.n, self.m)
+
+    def workspace_size(self):
+        b = ctypes.c_size_t()
+        _lib.check("gridspt_workspace_size", self.lib.gridspt_workspace_size(self.handle, ctypes.byref(b)))
+        return b.value
+
+    def _check_half(self, t, lead, name):
+        exp = self.half_shape(*lead)
+        if t.dtype != torch.complex64 or tuple(t.shape) != exp or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous CUDA complex64 {exp}, got {t.dtype} {tuple(t.shape)}")
+
+
+def linear_amplitude(cosmo=None):
+    lib = _lib.load()
+    c = _lib.GridsptCosmo(**(cosmo or DEFAULT_COSMO))
+    A = ctypes.c_double()
+    _lib.check("gridspt_linear_amplitude", lib.gridspt_linear_amplitude(ctypes.byref(c), ctypes.byref(A)))
+    return A.value
+
+
+def make_linear_field(plan, seeds, cosmo=None, out=None):
+    seeds = [int(s) for s in seeds]
+    if len(seeds) != plan.batch:
+        raise ValueError(f"need {plan.batch} seeds")
+    if out is None:
+        out = torch.empty(plan.half_shape(plan.batch), dtype=torch.complex64, device="cuda")
+    plan._check_half(out, (plan.batch,), "out")
+    c = _lib.GridsptCosmo(**(cosmo or DEFAULT_COSMO))
+    arr = (ctypes.c_uint64 * len(seeds))(*seeds)
+    _lib.check("gridspt_make_linear_field",
+               plan.lib.gridspt_make_linear_field(plan.handle, ctypes.byref(c), arr, _ptr(out), _stream()))
+    return out
+
+
+def run_orders(plan, delta1, start_order=2, spectra=None, ws=None):
+    plan._check_half(delta1, (plan.batch,), "delta1")
+    if spectra is None:
+        spectra = torch.empty(plan.half_shape(plan.batch, plan.n_max - 1, 2), dtype=torch.complex64, device="cuda")
+    plan._check_half(spectra, (plan.batch, plan.n_max - 1, 2), "spectra")
+    need = plan.workspace_size()
+    if ws is None:
+        ws = torch.empty(max(need, 16), dtype=torch.uint8, device="cuda")
+    _lib.check("gridspt_run_orders",
+               plan.lib.gridspt_run_orders(plan.handle, _ptr(delta1), start_order, _ptr(spectra), _ptr(ws),
+                                           ws.numel() * ws.element_size(), _stream()))
+    return spectra
+
+
+def c2r(plan, spec, out=None):
+    lead = tuple(spec.shape[:-3])
+    count = int(math.prod(lead)) if lead else 1
+    plan._check_half(spec, lead, "spec")
+    if out is None:
+        out = torch.empty(lead + (plan.n,) * 3, dtype=torch.float32, device="cuda")
+    _lib.check("gridspt_c2r", plan.lib.gridspt_c2r(plan.handle, _ptr(spec), _ptr(out), count, _stream()))
+    return out
+
+
+def r2c(plan, field, out=None):
+    lead = tuple(field.shape[:-3])
+    count = int(math.prod(lead)) if lead else 1
+    if field.dtype != torch.float32 or not field.is_contiguous() or tuple(field.shape[-3:]) != (plan.n,) * 3:
+        raise ValueError("field: expected contiguous float32 [..., N, N, N]")
+    if out is None:
+        out = torch.empty(plan.half_shape(*lead), dtype=torch.complex64, device="cuda")
+    _lib.check("gridspt_r2c", plan.lib.gridspt_r2c(plan.handle, _ptr(field), _ptr(out), count, _stream()))
+    return out
+
+
+def _edges(edges):
+    e = [float(x) for x in edges]
+    return (ctypes.c_double * len(e))(*e), len(e) - 1
+
+
+def power_workspace_size(plan, nbins):
+    b = ctypes.c_size_t()
+    _lib.check("gridspt_power_workspace_size",
+               plan.lib.gridspt_power_workspace_size(plan.handle, nbins, ctypes.byref(b)))
+    return b.value
+
+
+def power(plan, a, b, edges, ws=None, out=None, nk=None):
+    """P(i) = L^3 / N_i sum Re[a b*] over shell i; returns (p, n_k) device tensors."""
+    plan._check_half(a, (), "a")
+    plan._check_half(b, (), "b")
+    e, nb = _edges(edges)
+    if out is None:
+        out = torch.empty(nb, dtype=torch.float64, device="cuda")
+    if nk is None:
+        nk = torch.empty(nb, dtype=torch.int64, device="cuda")
+    if ws is None:
+        ws = torch.empty(power_workspace_size(plan, nb), dtype=torch.uint8, device="cuda")
+    _lib.check("gridspt_power",
+               plan.lib.gridspt_power(plan.handle, _ptr(a), _ptr(b), nb, e, _ptr(out), _ptr(nk), _ptr(ws),
+                                      ws.numel(), _stream()))
+    return out, nk
+
+
+def bispectrum_workspace_size(plan, nbins):
+    b = ctypes.c_size_t()
+    _lib.check("gridspt_bispectrum_workspace_size",
+               plan.lib.gridspt_bispectrum_workspace_size(plan.handle, nbins, ctypes.byref(b)))
+    return b.value
+
+
+def bispectrum(plan, a, b, edges, ws=None):
+    """Equilateral shell triple product E = L^6 sum I_a^2 I_b / sum J^3 and N_tri per
+    shell; B_tree = 3 E for a = delta_1, b = delta_2."""
+    plan._check_half(a, (), "a")
+    plan._check_half(b, (), "b")
+    e, nb = _edges(edges)
+    E = torch.empty(nb, dtype=torch.float64, device="cuda")
+    nt = torch.empty(nb, dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = torch.empty(bispectrum_workspace_size(plan, nb), dtype=torch.uint8, device="cuda")
+    _lib.check("gridspt_bispectrum",
+               plan.lib.gridspt_bispectrum(plan.handle, _ptr(a), _ptr(b), nb, e, _ptr(E), _ptr(nt), _ptr(ws),
+                                           ws.numel(), _stream()))
+    return E, nt
+
+
+def default_kcut(n, n_max, box):
+    """2 k_Ny / (n_max + 1) in h/Mpc."""
+    return 2.0 * math.pi / box * n / (n_max + 1)
+
+
+def profile_begin():
+    lib = _lib.load()
+    _lib.check("gridspt_profile_begin", lib.gridspt_profile_begin())
+
+
+def profile_end():
+    """{kernel kind: (launches, ms, algorithmic bytes)} recorded since profile_begin."""
+    lib = _lib.load()
+    cap = 32
+    arr = (_lib.GridsptKernelStat * cap)()
+    n = ctypes.c_int32()
+    _lib.check("gridspt_profile_end", lib.gridspt_profile_end(arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].ms, arr[i].bytes) for i in range(n.value)}

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 fields and transforms against FP64):
+* fields: RMS relative error over all modes (= over all cells, Parseval)
+  <= 1e-5 at n = 2 and <= 1e-4 at every n <= 5;
+* initial field: FP64 arithmetic rounded to FP32 on the GPU, so each mode within
+  2^-23 relative of the oracle (a few ulp of headroom);
+* shell power: <= 1e-5 relative per bin with N_k > 0 and |P| > 1e-3 max |P|;
+  N_k bit-exact (integer counting);
+* transforms alone: RMS relative error <= 2e-6.
+Inputs to the recursion are the oracle's FP64 initial field rounded to FP32, so
+that both sides start from the same numbers; nothing computed by the GPU is
+ever fed to the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import cosmology, estimators, spt  # noqa: E402
+from paper_1807_04215_gb300 import gridspt as g  # noqa: E402
+from tests import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+COSMO = cosmology.DEFAULT_COSMO
+
+
+def to_dev(full):
+    half = inputs.full_to_half(full).astype(np.complex64)
+    return torch.from_numpy(half).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def rms_rel(got_half, ref_full):
+    """Parseval-weighted RMS relative error of a half spectrum vs a full grid."""
+    N = ref_full.shape[0]
+    ref = ref_full[:, :, : N // 2]
+    w = np.full(ref.shape, 2.0)
+    w[:, :, 0] = 1.0
+    num = np.sum(w * np.abs(got_half - ref) ** 2)
+    den = np.sum(w * np.abs(ref) ** 2)
+    return math.sqrt(num / den)
+
+
+# ------------------------------------------------------------- initial field
+@pytest.mark.parametrize("N,L,n_max,seed", [(64, 500.0, 3, 1000), (48, 300.0, 5, 7), (12, 100.0, 2, 3)])
+def test_linear_field_matches_oracle(N, L, n_max, seed):
+    plan = g.Plan(N, n_max, L)
+    d1 = host(g.make_linear_field(plan, [seed])[0])
+    ref = spt.linear_field(N, L, n_max, COSMO, seed)[:, :, : N // 2]
+    assert np.array_equal(d1 != 0, ref != 0)          # identical cut / Nyquist decisions
+    assert np.abs(d1 - ref).max() <= 2.0 ** -23 * 4 * np.abs(ref).max()
+    nz = ref != 0
+    assert np.max(np.abs(d1[nz] - ref[nz]) / np.abs(ref[nz])) < 4e-7
+
+
+def test_linear_field_batch_uses_each_seed():
+    N, L = 32, 200.0
+    plan = g.Plan(N, 3, L, batch=3)
+    d = g.make_linear_field(plan, [5, 6, 7])
+    for b, s in enumerate([5, 6, 7]):
+        ref = spt.linear_field(N, L, 3, COSMO, s)[:, :, : N // 2]
+        assert np.abs(host(d[b]) - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------- transforms
+@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256])
+def test_c2r_matches_oracle(N):
+    plan = g.Plan(N, 2, 100.0)
+    full = spt.forward(inputs.random_real((N, N, N), N))
+    full[spt.nyquist_mask(N)] = 0
+    got = g.c2r(plan, to_dev(full)).cpu().numpy().astype(np.float64)
+    ref = spt.backward(full).real
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-6
+
+
+@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256])
+def test_r2c_matches_oracle(N):
+    plan = g.Plan(N, 2, 100.0)
+    x = inputs.random_real((2, N, N, N), 100 + N)
+    got = g.r2c(plan, torch.from_numpy(x.astype(np.float32)).cuda())
+    for f in range(2):
+        ref = spt.forward(x[f].astype(np.float32).astype(np.float64))
+        ref[spt.nyquist_mask(N)] = 0
+        assert rms_rel(host(got[f]), ref) < 2e-6
+
+
+def test_c2r_in_place_equals_out_of_place():
+    N = 64
+    plan = g.Plan(N, 2, 100.0)
+    full = spt.forward(inputs.random_real((N, N, N), 9))
+    full[spt.nyquist_mask(N)] = 0
+    a = to_dev(full)
+    out = g.c2r(plan, a)
+    b = a.clone()
+    g.c2r(plan, b, out=b.view(torch.float32).view(N, N, N))
+    assert torch.equal(out, b.view(torch.float32).view(N, N, N))
+
+
+# ------------------------------------------------------------- recursion
+def _parity_case(N, L, n_max, seed, kcut_nl=0.0, kcut_lin=0.0):
+    plan = g.Plan(N, n_max, L, kcut_lin=kcut_lin, kcut_nl=kcut_nl)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, seed, kcut_lin=kcut_lin or None)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))  # FP32-rounded input
+    spectra = g.run_orders(plan, to_dev(ref1)[None])
+    dk, tk = spt.run_orders(ref1, L, n_max, kcut_nl=kcut_nl or None)
+    errs = {}
+    for n in range(2, n_max + 1):
+        for which, ref in ((0, dk[n]), (1, tk[n])):
+            errs[(n, which)] = rms_rel(host(spectra[0, n - 2, which]), ref)
+    return errs
+
+
+@pytest.mark.parametrize("N,L,n_max,seed", [
+    (64, 500.0, 3, 1000),    # 64^3, L = 500, n_max = 3 workload
+    (32, 250.0, 4, 11),
+    (48, 300.0, 5, 12),      # radix-3 path, ragged tiles
+    (24, 150.0, 5, 13),
+    (96, 400.0, 3, 14),
+])
+def test_recursion_matches_oracle(N, L, n_max, seed):
+    errs = _parity_case(N, L, n_max, seed)
+    for (n, which), e in errs.items():
+        tol = 1e-5 if n == 2 else 1e-4
+        assert e < tol, (n, which, e)
+
+
+@pytest.mark.slow
+def test_recursion_matches_oracle_128_fifth_order():
+    errs = _parity_case(128, 500.0, 5, 21)
+    for (n, which), e in errs.items():
+        assert e < (1e-5 if n == 2 else 1e-4), (n, which, e)
+
+
+def test_recursion_with_nonlinear_cut_matches_oracle():
+    kF = 2 * math.pi / 300.0
+    errs = _parity_case(48, 300.0, 4, 31, kcut_nl=kF * 14.5, kcut_lin=kF * 9.0)
+    for (n, which), e in errs.items():
+        assert e < 1e-4, (n, which, e)
+
+
+def test_single_plane_wave_closed_form_on_gpu():
+    """Zel'dovich closed form of a 1D wave at every order (FP32 tolerance)."""
+    N, L, A = 32, 100.0, 0.1
+    plan = g.Plan(N, 5, L)
+    d1 = to_dev(inputs.plane_waves(N, [((1, 0, 0), A)]))[None]
+    spectra = g.run_orders(plan, d1)
+    for n in range(2, 6):
+        exp = np.zeros((N, N, N // 2), complex)
+        for m in range(n % 2, n + 1, 2):
+            j = (n - m) // 2
+            v = (-1) ** j * m ** n * (A / 2) ** n / (math.factorial(j) * math.factorial(m + j))
+            exp[m % N, 0, 0] = v
+            exp[-m % N, 0, 0] = v
+        for which in (0, 1):
+            got = host(spectra[0, n - 2, which])
+            assert np.abs(got - exp).max() < 1e-5 * (A / 2) ** n * 2 ** n, (n, which)
+
+
+def test_resume_equals_full_run_bitwise():
+    N, L, n_max = 64, 400.0, 5
+    plan = g.Plan(N, n_max, L)
+    d1 = g.make_linear_field(plan, [77])
+    full = g.run_orders(plan, d1)
+    part = full.clone()
+    part[:, 2:] = 0           # forget orders 4 and 5
+    g.run_orders(plan, d1, start_order=4, spectra=part)
+    assert torch.equal(full, part)
+
+
+def test_run_is_bitwise_repeatable_and_batched_equals_single():
+    N, L, n_max = 48, 300.0, 4
+    plan2 = g.Plan(N, n_max, L, batch=2)
+    d = g.make_linear_field(plan2, [1, 2])
+    a = g.run_orders(plan2, d)
+    b = g.run_orders(plan2, d)
+    assert torch.equal(a, b)
+    plan1 = g.Plan(N, n_max, L)
+    s = g.run_orders(plan1, d[1:2].contiguous())
+    assert torch.equal(a[1:2], s)
+
+
+def test_power_of_two_scaling_bitwise():
+    """delta_1 -> 2 delta_1 gives delta_n -> 2^n delta_n exactly (every step is
+    linear or a product, and scaling by 2 is exact in FP32)."""
+    N, L, n_max = 64, 500.0, 5
+    plan = g.Plan(N, n_max, L)
+    d1 = g.make_linear_field(plan, [3])
+    a = g.run_orders(plan, d1)
+    b = g.run_orders(plan, d1 * 2)
+    for n in range(2, n_max + 1):
+        assert torch.equal(b[:, n - 2], a[:, n - 2] * (2.0 ** n))
+
+
+# ------------------------------------------------------------- estimators
+def _bins_linear(L, nb):
+    kF = 2 * math.pi / L
+    return [kF * (b + 0.5) for b in range(nb + 1)]
+
+
+def _bins_log(lo, hi, nb):
+    return [lo * (hi / lo) ** (i / nb) for i in range(nb + 1)]
+
+
+@pytest.mark.parametrize("N,L,edges", [
+    (64, 500.0, _bins_linear(500.0, 16)),
+    (64, 1000.0, _bins_log(0.01, 0.19, 12)),
+    (48, 300.0, _bins_linear(300.0, 20)),
+])
+def test_power_matches_oracle(N, L, edges):
+    n_max = 3
+    plan = g.Plan(N, n_max, L)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, 5)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    d1 = to_dev(ref1)
+    spectra = g.run_orders(plan, d1[None])
+    dk, _ = spt.run_orders(ref1, L, n_max)
+    pairs = [(d1, d1, ref1, ref1), (spectra[0, 0, 0], spectra[0, 0, 0], dk[2], dk[2]),
+             (d1, spectra[0, 1, 0], ref1, dk[3])]
+    for a, b, ra, rb in pairs:
+        p, nk = g.power(plan, a, b, edges)
+        pr, nkr = estimators.power(ra, rb, L, edges)
+        assert np.array_equal(nk.cpu().numpy(), nkr)
+        p = p.cpu().numpy()
+        sel = (nkr > 0) & (np.abs(pr) > 1e-3 * np.abs(pr).max())
+        assert np.all(np.abs(p[sel] - pr[sel]) <= 1e-5 * np.abs(pr[sel])), np.abs(p[sel] / pr[sel] - 1).max()
+
+
+def test_power_is_bitwise_repeatable():
+    N, L = 64, 500.0
+    plan = g.Plan(N, 3, L)
+    d1 = g.make_linear_field(plan, [9])[0]
+    e = _bins_linear(L, 16)
+    a, _ = g.power(plan, d1, d1, e)
+    b, _ = g.power(plan, d1, d1, e)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("N,L,nb", [(32, 250.0, 6), (48, 300.0, 8)])
+def test_bispectrum_matches_oracle(N, L, nb):
+    n_max = 3
+    plan = g.Plan(N, n_max, L)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, 19)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    dk, _ = spt.run_orders(ref1, L, 2)
+    kc = 2 * math.pi / L * N / (n_max + 1)
+    edges = [kc * i / nb for i in range(nb + 1)]
+    d1 = to_dev(ref1)
+    d2 = to_dev(dk[2])
+    E, nt = g.bispectrum(plan, d1, d2, edges)
+    Er, ntr = estimators.bispectrum_equilateral(ref1, dk[2].astype(np.complex64).astype(np.complex128), L, edges)
+    nt = nt.cpu().numpy()
+    assert np.allclose(nt, ntr, rtol=1e-6, atol=1e-3)
+    E = E.cpu().numpy()
+    sel = ntr > 0.5
+    assert np.all(np.abs(E[sel] - Er[sel]) <= 1e-4 * np.abs(Er[sel]).max())
