@@ -14,8 +14,8 @@
 // and blocks are then summed in a fixed order: results are bitwise repeatable.
 //
 // Bispectrum (Eq. bk_tree, FFT shell estimator): sums over cells of
-// I_a(x)^2 I_b(x) and J(x)^3 in FP64 (four-cell FP32 partial products),
-// fixed-order block and grid reductions.
+// I_a(x)^2 I_b(x) and J(x)^3; each thread keeps a Kahan-compensated FP32 sum
+// of four-cell FP32 products, then FP64 fixed-order block and grid reductions.
 #include "gridspt_internal.h"
 
 namespace gridspt {
@@ -138,19 +138,28 @@ int bispec_blocks(const Geo& g) {
     return (int)(b < 1216 ? b : 1216);
 }
 
+// Kahan-compensated FP32 running sum (Kahan 1965): c carries the low-order
+// part lost by each addition.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 __global__ void __launch_bounds__(kBisThreads)
 k_bispec(const float4* __restrict__ ia, const float4* __restrict__ ib, const float4* __restrict__ jj,
          long long n4, double* __restrict__ partial) {
     __shared__ double r1[kBisThreads], r2[kBisThreads];
-    double s1 = 0.0, s2 = 0.0;
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
         const float4 a = ia[i], b = ib[i], j = jj[i];
-        s1 += (double)(a.x * a.x * b.x + a.y * a.y * b.y) + (double)(a.z * a.z * b.z + a.w * a.w * b.w);
-        s2 += (double)(j.x * j.x * j.x + j.y * j.y * j.y) + (double)(j.z * j.z * j.z + j.w * j.w * j.w);
+        kahan_add(s1, c1, (a.x * a.x * b.x + a.y * a.y * b.y) + (a.z * a.z * b.z + a.w * a.w * b.w));
+        kahan_add(s2, c2, (j.x * j.x * j.x + j.y * j.y * j.y) + (j.z * j.z * j.z + j.w * j.w * j.w));
     }
-    r1[threadIdx.x] = s1;
-    r2[threadIdx.x] = s2;
+    r1[threadIdx.x] = (double)s1 - (double)c1;
+    r2[threadIdx.x] = (double)s2 - (double)c2;
     __syncthreads();
     for (int h = kBisThreads / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) {

@@ -28,8 +28,8 @@ struct Cfg {
     // column passes (length N)
     static constexpr int EC = fft_elems(N);
     static constexpr int PC = N / EC;
-    static constexpr int TZC = cmin(cmin(16, cmax(8, 512 / PC)), 1024 / PC);
-    static constexpr int TZD = cmin(16, cmax(4, 512 / PC));  // fused derive pass
+    static constexpr int TZC = cmin(16, 1024 / PC);
+    static constexpr int TZD = cmin(16, 1024 / PC);  // fused derive pass
     // contiguous-axis passes (length M)
     static constexpr int EZ = fft_elems(M);
     static constexpr int PZ = M / EZ;
@@ -41,6 +41,51 @@ __device__ __forceinline__ int signed_idx(int n, int N) { return n < N / 2 ? n :
 
 __device__ __forceinline__ void load_table(float2* tw, const float2* __restrict__ twg, int N) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+}
+
+// Copy TZ contiguous rows of M float2 between global memory and a shared tile
+// of pitch PITCH. Every thread moves E/2 float4 (all loads issued before the
+// shared stores, so E/2 16-byte requests per thread are in flight).
+template <int M, int TZ, int PITCH, int NTHR>
+__device__ __forceinline__ void tile_load(float2* tile, const float2* src, long long row0, long long rows) {
+    constexpr int RV = M / 2;              // float4 per row
+    constexpr int NV = TZ * RV;
+    constexpr int PER = (NV + NTHR - 1) / NTHR;
+    float4 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        const int r = idx / RV, j = idx - r * RV;
+        const long long row = row0 + r;
+        v[u] = (idx < NV && row < rows) ? reinterpret_cast<const float4*>(src + row * M)[j]
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        if (idx < NV) {
+            const int r = idx / RV, j = idx - r * RV;
+            tile[r * PITCH + 2 * j] = make_float2(v[u].x, v[u].y);
+            tile[r * PITCH + 2 * j + 1] = make_float2(v[u].z, v[u].w);
+        }
+    }
+}
+
+template <int M, int TZ, int PITCH, int NTHR>
+__device__ __forceinline__ void tile_store(float2* dst, const float2* tile, long long row0, long long rows) {
+    constexpr int RV = M / 2;
+    constexpr int NV = TZ * RV;
+    constexpr int PER = (NV + NTHR - 1) / NTHR;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        const int r = idx / RV, j = idx - r * RV;
+        const long long row = row0 + r;
+        if (idx < NV && row < rows) {
+            const float2 a = tile[r * PITCH + 2 * j], b = tile[r * PITCH + 2 * j + 1];
+            reinterpret_cast<float4*>(dst + row * M)[j] = make_float4(a.x, a.y, b.x, b.y);
+        }
+    }
 }
 
 // ------------------------------------------------------------ column pass
@@ -91,17 +136,12 @@ k_zc2r(const float2* in, float2* out, long long fstride,
     float2* tw = sm;
     float2* tile = sm + N;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    const int nthr = TZ * P;
     load_table(tw, twg, N);
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
     const float2* src = in + blockIdx.y * fstride;
     float2* dst = out + blockIdx.y * fstride;
-    for (int idx = tid; idx < TZ * M; idx += nthr) {
-        const int r = idx / M, j = idx - r * M;
-        const long long row = row0 + r;
-        tile[r * PITCH + j] = row < rows ? src[row * M + j] : make_float2(0.f, 0.f);
-    }
+    tile_load<M, TZ, PITCH, TZ * P>(tile, src, row0, rows);
     __syncthreads();
     float2* colp = tile + c * PITCH;
     float2 x[E];
@@ -119,11 +159,7 @@ k_zc2r(const float2* in, float2* out, long long fstride,
 #pragma unroll
     for (int i = 0; i < E; ++i) colp[p + P * i] = x[i];
     __syncthreads();
-    for (int idx = tid; idx < TZ * M; idx += nthr) {
-        const int r = idx / M, j = idx - r * M;
-        const long long row = row0 + r;
-        if (row < rows) dst[row * M + j] = tile[r * PITCH + j];
-    }
+    tile_store<M, TZ, PITCH, TZ * P>(dst, tile, row0, rows);
 }
 
 // ------------------------------------------------ contiguous axis: R2C
@@ -136,17 +172,12 @@ k_zr2c(const float2* in, float2* out, long long fstride,
     float2* tw = sm;
     float2* tile = sm + N;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    const int nthr = TZ * P;
     load_table(tw, twg, N);
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
     const float2* src = in + blockIdx.y * fstride;
     float2* dst = out + blockIdx.y * fstride;
-    for (int idx = tid; idx < TZ * M; idx += nthr) {
-        const int r = idx / M, j = idx - r * M;
-        const long long row = row0 + r;
-        tile[r * PITCH + j] = row < rows ? src[row * M + j] : make_float2(0.f, 0.f);
-    }
+    tile_load<M, TZ, PITCH, TZ * P>(tile, src, row0, rows);
     __syncthreads();
     float2* colp = tile + c * PITCH;
     float2 x[E];
@@ -158,16 +189,25 @@ k_zr2c(const float2* in, float2* out, long long fstride,
     for (int i = 0; i < E; ++i) colp[p + P * i] = x[i];
     __syncthreads();
     const float half = 0.5f * scale;
-    for (int idx = tid; idx < TZ * M; idx += nthr) {
-        const int r = idx / M, k = idx - r * M;
+    constexpr int RV = M / 2, NV = TZ * RV, NTHR = TZ * P, PER = (NV + NTHR - 1) / NTHR;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = tid + u * NTHR;
+        const int r = idx / RV, j = idx - r * RV;
         const long long row = row0 + r;
-        if (row >= rows) continue;
-        const float2 Z = tile[r * PITCH + k];
-        const float2 Zr = cconj(tile[r * PITCH + (k ? M - k : 0)]);
-        const float2 S = cadd(Z, Zr);                 // 2 E[k]
-        const float2 t = cmul(cconj(tw[k]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
-        // X = E + e^{-2 pi i k / N} O = (S - i t) / 2
-        dst[row * M + k] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
+        if (idx >= NV || row >= rows) continue;
+        float2 X[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * j + h;
+            const float2 Z = tile[r * PITCH + k];
+            const float2 Zr = cconj(tile[r * PITCH + (k ? M - k : 0)]);
+            const float2 S = cadd(Z, Zr);                      // 2 E[k]
+            const float2 t = cmul(cconj(tw[k]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
+            // X = E + e^{-2 pi i k / N} O = (S - i t) / 2
+            X[h] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
+        }
+        reinterpret_cast<float4*>(dst + row * M)[j] = make_float4(X[0].x, X[0].y, X[1].x, X[1].y);
     }
 }
 
