@@ -105,16 +105,31 @@ k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins
     }
 }
 
-__global__ void k_power_final(const double* __restrict__ partial, int G, int nb, double vol,
-                              double* __restrict__ p_out, int64_t* __restrict__ nk_out) {
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-        double s = 0.0, c = 0.0;
-        for (int g = 0; g < G; ++g) {
-            s += partial[(long long)g * 2 * nb + t];
-            c += partial[(long long)g * 2 * nb + nb + t];
+// One block per bin: thread t sums partials t, t + 256, ... in order, then a
+// fixed shared-memory tree; bitwise repeatable.
+__global__ void __launch_bounds__(256)
+k_power_final(const double* __restrict__ partial, int G, int nb, double vol,
+              double* __restrict__ p_out, int64_t* __restrict__ nk_out) {
+    __shared__ double rs[256], rc[256];
+    const int t = blockIdx.x;
+    double s = 0.0, c = 0.0;
+    for (int g = threadIdx.x; g < G; g += 256) {
+        s += partial[(long long)g * 2 * nb + t];
+        c += partial[(long long)g * 2 * nb + nb + t];
+    }
+    rs[threadIdx.x] = s;
+    rc[threadIdx.x] = c;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            rs[threadIdx.x] += rs[threadIdx.x + h];
+            rc[threadIdx.x] += rc[threadIdx.x + h];
         }
-        p_out[t] = c > 0.0 ? vol * s / c : 0.0;
-        if (nk_out) nk_out[t] = (int64_t)(c + 0.5);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        p_out[t] = rc[0] > 0.0 ? vol * rs[0] / rc[0] : 0.0;
+        if (nk_out) nk_out[t] = (int64_t)(rc[0] + 0.5);
     }
 }
 
@@ -125,7 +140,7 @@ cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const B
     k_power<<<G, kPowWarps * 32, 0, s>>>(a, b, bins, g.N, g.M, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_power_final<<<1, 64, 0, s>>>(partial, G, bins.nbins, volume, p_out, nk_out);
+    k_power_final<<<bins.nbins, 256, 0, s>>>(partial, G, bins.nbins, volume, p_out, nk_out);
     return cudaGetLastError();
 }
 
@@ -174,17 +189,30 @@ k_bispec(const float4* __restrict__ ia, const float4* __restrict__ ib, const flo
     }
 }
 
-__global__ void k_bispec_final(const double* __restrict__ partial, int G, double vol2, double cells,
-                               double* __restrict__ e_out, double* __restrict__ ntri_out) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(256)
+k_bispec_final(const double* __restrict__ partial, int G, double vol2, double cells,
+               double* __restrict__ e_out, double* __restrict__ ntri_out) {
+    __shared__ double r1[256], r2[256];
     double s1 = 0.0, s2 = 0.0;
-    for (int g = 0; g < G; ++g) {
+    for (int g = threadIdx.x; g < G; g += 256) {
         s1 += partial[2 * g];
         s2 += partial[2 * g + 1];
     }
-    const double nt = s2 / cells;
-    *ntri_out = nt;
-    *e_out = nt > 0.5 ? vol2 * s1 / s2 : 0.0;
+    r1[threadIdx.x] = s1;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            r1[threadIdx.x] += r1[threadIdx.x + h];
+            r2[threadIdx.x] += r2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nt = r2[0] / cells;
+        *ntri_out = nt;
+        *e_out = nt > 0.5 ? vol2 * r1[0] / r2[0] : 0.0;
+    }
 }
 
 cudaError_t launch_bispec_reduce(const Geo& g, const float* ia, const float* ib, const float* j,
@@ -197,7 +225,7 @@ cudaError_t launch_bispec_reduce(const Geo& g, const float* ia, const float* ib,
                                        reinterpret_cast<const float4*>(j), n4, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_bispec_final<<<1, 32, 0, s>>>(partial, G, vol2, (double)g.N * g.N * g.N, e_out, ntri_out);
+    k_bispec_final<<<1, 256, 0, s>>>(partial, G, vol2, (double)g.N * g.N * g.N, e_out, ntri_out);
     return cudaGetLastError();
 }
 

@@ -33,8 +33,10 @@ struct Cfg {
     // contiguous-axis passes (length M)
     static constexpr int EZ = fft_elems(M);
     static constexpr int PZ = M / EZ;
-    static constexpr int TZZ = cmin(64, cmax(1, 256 / PZ));
-    static constexpr int PITCH = M + 1;  // odd pitch: conflict-free column access
+    // 16 rows or more per block: a warp then spans 16 rows of the odd-pitch
+    // tile, so column accesses of a warp hit 16 distinct 8-byte bank pairs
+    static constexpr int TZZ = cmin(cmin(64, cmax(16, 256 / PZ)), 1024 / PZ);
+    static constexpr int PITCH = M + 1;
 };
 
 __device__ __forceinline__ int signed_idx(int n, int N) { return n < N / 2 ? n : n - N; }
@@ -44,47 +46,41 @@ __device__ __forceinline__ void load_table(float2* tw, const float2* __restrict_
 }
 
 // Copy TZ contiguous rows of M float2 between global memory and a shared tile
-// of pitch PITCH. Every thread moves E/2 float4 (all loads issued before the
-// shared stores, so E/2 16-byte requests per thread are in flight).
+// of odd pitch PITCH. Consecutive threads move consecutive float2 of a row
+// (coalesced, conflict-free); all loads are issued before the shared stores,
+// so each thread has TZ * M / NTHR requests in flight.
 template <int M, int TZ, int PITCH, int NTHR>
 __device__ __forceinline__ void tile_load(float2* tile, const float2* src, long long row0, long long rows) {
-    constexpr int RV = M / 2;              // float4 per row
-    constexpr int NV = TZ * RV;
+    constexpr int NV = TZ * M;
     constexpr int PER = (NV + NTHR - 1) / NTHR;
-    float4 v[PER];
+    float2 v[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NTHR;
-        const int r = idx / RV, j = idx - r * RV;
+        const int r = idx / M, j = idx - r * M;
         const long long row = row0 + r;
-        v[u] = (idx < NV && row < rows) ? reinterpret_cast<const float4*>(src + row * M)[j]
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = (idx < NV && row < rows) ? src[row * M + j] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NTHR;
         if (idx < NV) {
-            const int r = idx / RV, j = idx - r * RV;
-            tile[r * PITCH + 2 * j] = make_float2(v[u].x, v[u].y);
-            tile[r * PITCH + 2 * j + 1] = make_float2(v[u].z, v[u].w);
+            const int r = idx / M, j = idx - r * M;
+            tile[r * PITCH + j] = v[u];
         }
     }
 }
 
 template <int M, int TZ, int PITCH, int NTHR>
 __device__ __forceinline__ void tile_store(float2* dst, const float2* tile, long long row0, long long rows) {
-    constexpr int RV = M / 2;
-    constexpr int NV = TZ * RV;
+    constexpr int NV = TZ * M;
     constexpr int PER = (NV + NTHR - 1) / NTHR;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NTHR;
-        const int r = idx / RV, j = idx - r * RV;
+        const int r = idx / M, j = idx - r * M;
         const long long row = row0 + r;
-        if (idx < NV && row < rows) {
-            const float2 a = tile[r * PITCH + 2 * j], b = tile[r * PITCH + 2 * j + 1];
-            reinterpret_cast<float4*>(dst + row * M)[j] = make_float4(a.x, a.y, b.x, b.y);
-        }
+        if (idx < NV && row < rows) dst[row * M + j] = tile[r * PITCH + j];
     }
 }
 
@@ -189,25 +185,19 @@ k_zr2c(const float2* in, float2* out, long long fstride,
     for (int i = 0; i < E; ++i) colp[p + P * i] = x[i];
     __syncthreads();
     const float half = 0.5f * scale;
-    constexpr int RV = M / 2, NV = TZ * RV, NTHR = TZ * P, PER = (NV + NTHR - 1) / NTHR;
+    constexpr int NV = TZ * M, NTHR = TZ * P, PER = (NV + NTHR - 1) / NTHR;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = tid + u * NTHR;
-        const int r = idx / RV, j = idx - r * RV;
+        const int r = idx / M, k = idx - r * M;
         const long long row = row0 + r;
         if (idx >= NV || row >= rows) continue;
-        float2 X[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = 2 * j + h;
-            const float2 Z = tile[r * PITCH + k];
-            const float2 Zr = cconj(tile[r * PITCH + (k ? M - k : 0)]);
-            const float2 S = cadd(Z, Zr);                      // 2 E[k]
-            const float2 t = cmul(cconj(tw[k]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
-            // X = E + e^{-2 pi i k / N} O = (S - i t) / 2
-            X[h] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
-        }
-        reinterpret_cast<float4*>(dst + row * M)[j] = make_float4(X[0].x, X[0].y, X[1].x, X[1].y);
+        const float2 Z = tile[r * PITCH + k];
+        const float2 Zr = cconj(tile[r * PITCH + (k ? M - k : 0)]);
+        const float2 S = cadd(Z, Zr);                      // 2 E[k]
+        const float2 t = cmul(cconj(tw[k]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
+        // X = E + e^{-2 pi i k / N} O = (S - i t) / 2
+        dst[row * M + k] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
     }
 }
 
@@ -286,7 +276,7 @@ k_derive(DeriveArgs args, const float2* __restrict__ twg, float kF, float inv_kF
                 const float g = s2 ? (float)(sa * sb) / (float)s2 : 0.f;
                 r = make_float2(g * v.x, g * v.y);
             } else {  // DK_SHELL
-                const bool in = (long long)s2 >= args.shell_lo && (long long)s2 < args.shell_hi;
+                const bool in = s2 > 0 && (long long)s2 >= args.shell_lo && (long long)s2 < args.shell_hi;
                 r = in ? v : make_float2(0.f, 0.f);
             }
             y[i] = r;
