@@ -146,6 +146,26 @@ gridspt_status gridspt_power(gridspt_plan plan, const void* a_k, const void* b_k
                              const double* edges, double* p_out, int64_t* nk_out, void* ws,
                              size_t ws_bytes, gridspt_stream stream);
 
+/* Allocation-free variant of gridspt_power for callers that cannot allocate
+ * device memory when they need a spectrum (their framework's allocator owns the
+ * device memory, or they are handed only input and output buffers). The paper
+ * has no counterpart: this is a deployment convenience.
+ * Same arguments and results as gridspt_power, without ws/ws_bytes: the
+ * per-block partial sums live in a static device array compiled into the
+ * library, 1,245,184 bytes (1216 blocks x 2 x 64 bins x 8 bytes), held on every
+ * GPU that loads the library until the process exits. Requests that would need
+ * more (nbins > 64) are rejected with GRIDSPT_E_INVALID and a message.
+ * The first call on each device looks up the array's device address (a host
+ * call, made with that device current); make that first call before any
+ * stream capture. No call allocates or frees memory. All calls on a device
+ * share the one array: each call overwrites every partial sum it reads, so no
+ * state carries over, but calls that can overlap on the GPU (different
+ * streams, no ordering between them) race on it and must be serialised by the
+ * caller. */
+gridspt_status gridspt_power_noalloc(gridspt_plan plan, const void* a_k, const void* b_k, int32_t nbins,
+                                     const double* edges, double* p_out, int64_t* nk_out,
+                                     gridspt_stream stream);
+
 /* Equilateral FFT shell bispectrum (Sec. III.B.1, Eq. bk_tree, measured with
  * an FFT shell estimator): for shell i,
  *   e_out[i]    = L^6 sum_x I_i[a](x)^2 I_i[b](x) / sum_x J_i(x)^3,

@@ -41,6 +41,8 @@ SIGNATURES = {
     "gridspt_power_workspace_size": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t)]),
     "gridspt_power": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
                                 c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gridspt_power_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
+                                        c_void_p, c_void_p, c_void_p]),
     "gridspt_bispectrum_workspace_size": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t)]),
     "gridspt_bispectrum": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -516,6 +516,30 @@ gridspt_status gridspt_power(gridspt_plan p, const void* a_k, const void* b_k, i
     return GRIDSPT_OK;
 }
 
+gridspt_status gridspt_power_noalloc(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins,
+                                     const double* edges, double* p_out, int64_t* nk_out,
+                                     gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!a_k || !b_k || !p_out) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!aligned16(a_k) || !aligned16(b_k)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    if (!power_static_fits(p->geo, nbins))
+        return fail(GRIDSPT_E_INVALID, "nbins=%d exceeds the %zu-byte static scratch (at most %d bins)", nbins,
+                    power_static_scratch_bytes(), kMaxBins);
+    BinSpec bs{};
+    if (gridspt_status st = make_bins(p, nbins, edges, 0, &bs)) return st;
+    const long long half = p->geo.N / 2;
+    if (bs.thr[nbins] > half * half) return fail(GRIDSPT_E_INVALID, "last edge above the Nyquist wavenumber");
+    if (gridspt_status st = set_device(p)) return st;
+    double* scratch = nullptr;
+    CK(power_static_scratch(&scratch), "static scratch address");
+    const double vol = p->d.box * p->d.box * p->d.box;
+    CKP(PK_POWER, power_bytes(p, bs.thr[nbins], a_k == b_k), (cudaStream_t)stream,
+        launch_power(p->geo, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k), bs, scratch,
+                     p_out, nk_out, vol, (cudaStream_t)stream), "power launch");
+    return GRIDSPT_OK;
+}
+
 namespace {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }

@@ -99,4 +99,11 @@ cudaError_t launch_bispec_reduce(const Geo& g, const float* ia, const float* ib,
 
 bool supported_n(int N);
 
+// Library-owned scratch of the allocation-free power entry point
+// (k_power_static.cu): device address of the static array on the current
+// device (looked up once per device), its size, and whether a request fits.
+cudaError_t power_static_scratch(double** out);
+size_t power_static_scratch_bytes();
+bool power_static_fits(const Geo& g, int nbins);
+
 }  // namespace gridspt

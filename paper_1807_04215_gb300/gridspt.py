@@ -159,6 +159,23 @@ def power(plan, a, b, edges, ws=None, out=None, nk=None):
     return out, nk
 
 
+def power_noalloc(plan, a, b, edges, out=None, nk=None):
+    """gridspt_power_noalloc: the shell power estimator with the library's own
+    static scratch, for callers that must not allocate device memory (the
+    caller passes only inputs and outputs)."""
+    plan._check_half(a, (), "a")
+    plan._check_half(b, (), "b")
+    e, nb = _edges(edges)
+    if out is None:
+        out = torch.empty(nb, dtype=torch.float64, device="cuda")
+    if nk is None:
+        nk = torch.empty(nb, dtype=torch.int64, device="cuda")
+    _lib.check("gridspt_power_noalloc",
+               plan.lib.gridspt_power_noalloc(plan.handle, _ptr(a), _ptr(b), nb, e, _ptr(out), _ptr(nk),
+                                              _stream()))
+    return out, nk
+
+
 def bispectrum_workspace_size(plan, nbins):
     b = ctypes.c_size_t()
     _lib.check("gridspt_bispectrum_workspace_size",
