@@ -239,7 +239,7 @@ def run_gpu(args, rank, world):
     kname, (nl, kms, kbytes) = max(prof.items(), key=lambda kv: kv[1][1])
     peak, src = peaks()
     achieved = kbytes / (kms / 1e3) / 1e9
-    rec_kinds = ("ic", "derive_x_inv", "derive_x_fwd_inv", "y_inv", "y_fwd", "x_fwd", "z_c2r", "z_r2c", "product")
+    rec_kinds = ("ic", "x_expand", "x_fwd_expand", "y_expand", "z_expand", "y_fwd", "x_fwd", "z_r2c", "product")
     breakdown = {k: {"launches": v[0], "ms_per_step": round(v[1] / args.steps, 3),
                      "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}

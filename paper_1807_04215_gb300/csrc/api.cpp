@@ -56,12 +56,12 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 // ------------------------------------------------------------- profiling
 enum ProfKind {
-    PK_IC, PK_DERIVE_INV, PK_DERIVE_FWD, PK_Y_INV, PK_Y_FWD, PK_X_FWD, PK_ZC2R, PK_ZR2C,
-    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_COUNT
+    PK_IC, PK_XEXP, PK_XEXP_FWD, PK_YEXP, PK_ZEXP, PK_Y_FWD, PK_X_FWD, PK_ZR2C,
+    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {
-    "ic", "derive_x_inv", "derive_x_fwd_inv", "y_inv", "y_fwd", "x_fwd", "z_c2r", "z_r2c",
-    "product", "power", "bispec_reduce"};
+    "ic", "x_expand", "x_fwd_expand", "y_expand", "z_expand", "y_fwd", "x_fwd", "z_r2c",
+    "product", "power", "bispec_reduce", "shell_x", "shell_y", "shell_z"};
 constexpr size_t kMaxProfRecs = 65536;
 
 struct ProfRec {
@@ -117,9 +117,11 @@ cudaError_t prof_launch(int kind, double bytes, cudaStream_t s, F&& f) {
 long long field_floats(const gridspt_plan_s* p) { return (long long)p->geo.N * p->geo.N * p->geo.N; }
 long long field_c(const gridspt_plan_s* p) { return (long long)p->geo.N * p->geo.N * p->geo.M; }
 
-int derived_count(int m) { return m == 1 ? 13 : 17; }
 int order_base(int m) { return m == 1 ? 0 : 13 + 17 * (m - 2); }
 int total_derived(int n_max) { return n_max >= 2 ? order_base(n_max) : 0; }
+// scratch of one derivative expansion: 7 x-fields + 12 xy-fields
+constexpr int kExpScratch = 7 + 12;
+int workspace_fields(int n_max) { return n_max >= 2 ? total_derived(n_max) + kExpScratch : 0; }
 
 // s2 threshold: smallest integer t >= 0 with kF * sqrt(t) >= e (FP64), so that
 // "t <= |s|^2" is exactly the FP64 test "e <= kF sqrt(|s|^2)".
@@ -276,7 +278,7 @@ gridspt_status gridspt_plan_destroy(gridspt_plan p) {
 
 gridspt_status gridspt_workspace_size(gridspt_plan p, size_t* bytes) {
     if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
-    *bytes = (size_t)total_derived(p->d.n_max) * (size_t)field_floats(p) * sizeof(float);
+    *bytes = (size_t)workspace_fields(p->d.n_max) * (size_t)field_floats(p) * sizeof(float);
     return GRIDSPT_OK;
 }
 
@@ -313,43 +315,128 @@ gridspt_status gridspt_make_linear_field(gridspt_plan p, const gridspt_cosmo* c,
 
 namespace {
 
-// Derived fields of order m from its spectra (delta_m, theta_m), written to
-// ws at the order's slot, through the backward x, y, z passes. With fwd, the
-// spectra buffers hold the y-transformed product output and the x pass first
-// completes the forward transform (writing delta_m(k), theta_m(k) in place).
+// Derived fields of order m from its spectra (Sec. II.C steps (2)/(5)),
+// written to ws at the order's slot, through the factorised x, y and z
+// expansion passes. With fwd, the spectra buffers hold the y-transformed
+// product output and the x pass first completes the forward transform
+// (writing delta_m(k), theta_m(k) in place).
+//
+// Order m >= 2, 17 real fields in slot order [delta, theta, d delta (3),
+// d theta (3), u (3), d_a u_b (xx, yy, zz, xy, xz, yz)], phi = theta / k^2:
+//   x-fields: X0 delta, X1 kx delta, X2 theta, X3 kx theta, X4 phi, X5 kx phi, X6 kx^2 phi
+//   xy-fields: Y0 X0, Y1 ky X0, Y2 X1, Y3 X2, Y4 ky X2, Y5 X3, Y6 X4, Y7 ky X4, Y8 ky^2 X4,
+//              Y9 X5, Y10 ky X5, Y11 X6
+//   real: delta = Y0, d_z delta = i kz Y0, d_y delta = i Y1, d_x delta = i Y2, theta = Y3,
+//         d_z theta = i kz Y3, d_y theta = i Y4, d_x theta = i Y5, u_z = -i kz Y6,
+//         d_z u_z = kz^2 Y6, u_y = -i Y7, d_y u_z = kz Y7, d_y u_y = Y8, u_x = -i Y9,
+//         d_x u_z = kz Y9, d_x u_y = Y10, d_x u_x = Y11.
+// Order 1 (theta = delta), 13 fields [delta, d delta (3), u (3), d_a u_b (6)]:
+//   x-fields: X0 delta, X1 kx delta, X2 phi, X3 kx phi, X4 kx^2 phi
+//   xy-fields: Y0 X0, Y1 ky X0, Y2 X1, Y3 X2, Y4 ky X2, Y5 ky^2 X2, Y6 X3, Y7 ky X3, Y8 X4
 gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* tk, float* ws,
                             bool fwd, cudaStream_t s) {
-    DeriveArgs a{};
-    a.src0 = dk;
-    a.src1 = tk;
     const long long F = field_c(p);
-    float2* out = reinterpret_cast<float2*>(ws + (long long)order_base(m) * field_floats(p));
-    a.out = out;
-    a.out_stride = F;
-    a.fwd_first = fwd ? 1 : 0;
-    a.s2_nl = p->s2_nl;
-    int k = 0;
-    if (m == 1) {
-        a.codes[k++] = derive_code(DK_ONE, 0, 0, 0);
-        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_IK, c, 0, 0);
-        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_NEG_IK_K2, c, 0, 0);
-    } else {
-        a.codes[k++] = derive_code(DK_ONE, 0, 0, 0);
-        a.codes[k++] = derive_code(DK_ONE, 0, 0, 1);
-        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_IK, c, 0, 0);
-        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_IK, c, 0, 1);
-        for (int c = 0; c < 3; ++c) a.codes[k++] = derive_code(DK_NEG_IK_K2, c, 0, 1);
-    }
-    const int src_t = m == 1 ? 0 : 1;
-    const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-    for (int t = 0; t < 6; ++t) a.codes[k++] = derive_code(DK_KK_K2, pairs[t][0], pairs[t][1], src_t);
-    a.nout = k;
     const double fb = 4.0 * (double)field_floats(p);  // bytes of one field
+    float2* real = reinterpret_cast<float2*>(ws + (long long)order_base(m) * field_floats(p));
+    float2* xs = reinterpret_cast<float2*>(ws + (long long)total_derived(p->d.n_max) * field_floats(p));
+    float2* ys = xs + 7 * F;
+    XExpArgs xa{};
+    xa.src0 = dk;
+    xa.src1 = tk;
+    xa.out = xs;
+    xa.out_stride = F;
+    xa.fwd_first = fwd ? 1 : 0;
+    xa.s2_nl = p->s2_nl;
+    YZExpArgs ya{}, za{};
+    ya.in = xs;
+    ya.in_stride = F;
+    ya.out = ys;
+    ya.out_stride = F;
+    za.in = ys;
+    za.in_stride = F;
+    za.out = real;
+    za.out_stride = F;
+    const int I = 1, NI = 2;  // z-pass constants i and -i
+    if (m == 1) {
+        const int xc[5] = {x_code(XK_POW, 0, XS_DELTA), x_code(XK_POW, 1, XS_DELTA), x_code(XK_POW, 0, XS_PHI),
+                           x_code(XK_POW, 1, XS_PHI), x_code(XK_POW, 2, XS_PHI)};
+        const int yc[9] = {y_code(0, 0, 0), y_code(0, 1, 1), y_code(1, 0, 2), y_code(2, 0, 3), y_code(2, 1, 4),
+                           y_code(2, 2, 5), y_code(3, 0, 6), y_code(3, 1, 7), y_code(4, 0, 8)};
+        const int zc[13] = {z_code(0, 0, 0, 0), z_code(0, 1, I, 3), z_code(1, 0, I, 2), z_code(2, 0, I, 1),
+                            z_code(3, 1, NI, 6), z_code(3, 2, 0, 9), z_code(4, 0, NI, 5), z_code(4, 1, 0, 12),
+                            z_code(5, 0, 0, 8), z_code(6, 0, NI, 4), z_code(6, 1, 0, 11), z_code(7, 0, 0, 10),
+                            z_code(8, 0, 0, 7)};
+        xa.nout = 5;
+        ya.nout = 9;
+        za.nout = 13;
+        for (int i = 0; i < 5; ++i) xa.codes[i] = xc[i];
+        for (int i = 0; i < 9; ++i) ya.codes[i] = yc[i];
+        for (int i = 0; i < 13; ++i) za.codes[i] = zc[i];
+    } else {
+        const int xc[7] = {x_code(XK_POW, 0, XS_DELTA), x_code(XK_POW, 1, XS_DELTA), x_code(XK_POW, 0, XS_THETA),
+                           x_code(XK_POW, 1, XS_THETA), x_code(XK_POW, 0, XS_PHI), x_code(XK_POW, 1, XS_PHI),
+                           x_code(XK_POW, 2, XS_PHI)};
+        const int yc[12] = {y_code(0, 0, 0), y_code(0, 1, 1), y_code(1, 0, 2), y_code(2, 0, 3),
+                            y_code(2, 1, 4), y_code(3, 0, 5), y_code(4, 0, 6), y_code(4, 1, 7),
+                            y_code(4, 2, 8), y_code(5, 0, 9), y_code(5, 1, 10), y_code(6, 0, 11)};
+        const int zc[17] = {z_code(0, 0, 0, 0), z_code(0, 1, I, 4), z_code(1, 0, I, 3), z_code(2, 0, I, 2),
+                            z_code(3, 0, 0, 1), z_code(3, 1, I, 7), z_code(4, 0, I, 6), z_code(5, 0, I, 5),
+                            z_code(6, 1, NI, 10), z_code(6, 2, 0, 13), z_code(7, 0, NI, 9), z_code(7, 1, 0, 16),
+                            z_code(8, 0, 0, 12), z_code(9, 0, NI, 8), z_code(9, 1, 0, 15), z_code(10, 0, 0, 14),
+                            z_code(11, 0, 0, 11)};
+        xa.nout = 7;
+        ya.nout = 12;
+        za.nout = 17;
+        for (int i = 0; i < 7; ++i) xa.codes[i] = xc[i];
+        for (int i = 0; i < 12; ++i) ya.codes[i] = yc[i];
+        for (int i = 0; i < 17; ++i) za.codes[i] = zc[i];
+    }
     const int nin = m == 1 ? 1 : 2;
-    CKP(fwd ? PK_DERIVE_FWD : PK_DERIVE_INV, fb * (fwd ? 2 * nin + k : nin + k), s,
-        launch_derive(p->geo, a, s), "derive launch");
-    CKP(PK_Y_INV, 2 * fb * k, s, launch_colpass(p->geo, out, F, k, 1, +1, 0, -1, s), "y pass");
-    CKP(PK_ZC2R, 2 * fb * k, s, launch_zc2r(p->geo, out, out, F, k, s), "z c2r");
+    CKP(fwd ? PK_XEXP_FWD : PK_XEXP, fb * (fwd ? 2 * nin + xa.nout : nin + xa.nout), s,
+        launch_xexp(p->geo, xa, s), "x expansion");
+    CKP(PK_YEXP, fb * (xa.nout + ya.nout), s, launch_yexp(p->geo, ya, s), "y expansion");
+    CKP(PK_ZEXP, fb * (ya.nout + za.nout), s, launch_zexp(p->geo, za, s), "z expansion");
+    return GRIDSPT_OK;
+}
+
+// Backward transform of `count` fields in place (or in -> out): x, y, z passes
+// with one output per input, optionally with a shell mask (bispectrum).
+gridspt_status backward_fields(const gridspt_plan_s* p, const float2* in0, const float2* in1, float2* out,
+                               long long out_stride, int count, bool shell, long long lo, long long hi,
+                               int band, bool skip_z, cudaStream_t s) {
+    const double fb = 4.0 * (double)field_floats(p);
+    XExpArgs xa{};
+    xa.src0 = const_cast<float2*>(in0);
+    xa.src1 = const_cast<float2*>(in1);
+    xa.out = out;
+    xa.out_stride = out_stride;
+    xa.s2_nl = -1;
+    xa.shell_lo = lo;
+    xa.shell_hi = hi;
+    xa.band = band;
+    xa.nout = count;
+    const int srcs[3] = {XS_DELTA, in1 == in0 ? XS_DELTA : XS_THETA, XS_ONE};
+    for (int f = 0; f < count; ++f) xa.codes[f] = x_code(shell ? XK_SHELL : XK_POW, 0, srcs[f]);
+    YZExpArgs ya{};
+    ya.in = out;
+    ya.in_stride = out_stride;
+    ya.out = out;
+    ya.out_stride = out_stride;
+    ya.nout = count;
+    ya.band = band;
+    for (int f = 0; f < count; ++f) ya.codes[f] = y_code(f, 0, f);
+    YZExpArgs za = ya;
+    za.band = 0;
+    for (int f = 0; f < count; ++f) za.codes[f] = z_code(f, 0, 0, f);
+    const int nin = in1 == in0 ? 1 : 2;
+    // algorithmic bytes: with a band B only the band columns move
+    const double N = p->geo.N, M = p->geo.M;
+    const double fx = band > 0 ? (2.0 * band - 1.0) * band / (N * M) : 1.0;   // x columns
+    const double fy_in = band > 0 ? (2.0 * band - 1.0) / N * band / M : 1.0;   // y inputs
+    const double fy_out = band > 0 ? band / M : 1.0;                         // y outputs
+    CKP(shell ? PK_BX : PK_XEXP, fb * fx * (nin + count), s, launch_xexp(p->geo, xa, s), "x pass");
+    CKP(shell ? PK_BY : PK_YEXP, fb * count * (fy_in + fy_out), s, launch_yexp(p->geo, ya, s), "y pass");
+    if (!skip_z) CKP(shell ? PK_BZ : PK_ZEXP, 2 * fb * count, s, launch_zexp(p->geo, za, s), "z pass");
     return GRIDSPT_OK;
 }
 
@@ -398,11 +485,11 @@ gridspt_status gridspt_run_orders(gridspt_plan p, const void* delta1_k, int32_t 
             const double fb = 4.0 * (double)field_floats(p);
             CKP(PK_PRODUCT, fb * (order_base(n) + 2), s, launch_product(p->geo, pa, s), "product launch");
             CKP(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, spec(n, 0), spec(n, 0), F, 2, 1.0f, s), "z r2c");
-            CKP(PK_Y_FWD, 4 * fb, s, launch_colpass(p->geo, spec(n, 0), F, 2, 1, -1, 0, -1, s), "y pass fwd");
+            CKP(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, spec(n, 0), F, 2, 1, 0, -1, s), "y pass fwd");
             if (n < n_max) {
                 if (gridspt_status st = derive_order(p, n, spec(n, 0), spec(n, 1), w, true, s)) return st;
             } else {
-                CKP(PK_X_FWD, 4 * fb, s, launch_colpass(p->geo, spec(n, 0), F, 2, 0, -1, 1, p->s2_nl, s),
+                CKP(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, spec(n, 0), F, 2, 0, 1, p->s2_nl, s),
                     "x pass fwd");
             }
         }
@@ -419,18 +506,11 @@ gridspt_status gridspt_c2r(gridspt_plan p, const void* in_k, float* out_x, int32
     cudaStream_t s = (cudaStream_t)stream;
     const long long F = field_c(p);
     for (int f = 0; f < count; ++f) {
-        DeriveArgs a{};
-        a.src0 = a.src1 = const_cast<float2*>(static_cast<const float2*>(in_k)) + f * F;
-        a.out = reinterpret_cast<float2*>(out_x) + f * F;
-        a.out_stride = F;
-        a.nout = 1;
-        a.codes[0] = derive_code(DK_ONE, 0, 0, 0);
-        a.s2_nl = -1;
-        CK(launch_derive(p->geo, a, s), "x pass");
+        const float2* in = static_cast<const float2*>(in_k) + f * F;
+        if (gridspt_status st = backward_fields(p, in, in, reinterpret_cast<float2*>(out_x) + f * F, F, 1, false, 0, 0,
+                                                0, false, s))
+            return st;
     }
-    float2* o = reinterpret_cast<float2*>(out_x);
-    CK(launch_colpass(p->geo, o, F, count, 1, +1, 0, -1, s), "y pass");
-    CK(launch_zc2r(p->geo, o, o, F, count, s), "z c2r");
     return GRIDSPT_OK;
 }
 
@@ -445,8 +525,8 @@ gridspt_status gridspt_r2c(gridspt_plan p, const float* in_x, void* out_k, int32
     float2* o = static_cast<float2*>(out_k);
     const float scale = (float)(1.0 / (double)field_floats(p));
     CK(launch_zr2c(p->geo, reinterpret_cast<const float2*>(in_x), o, F, count, scale, s), "z r2c");
-    CK(launch_colpass(p->geo, o, F, count, 1, -1, 0, -1, s), "y pass");
-    CK(launch_colpass(p->geo, o, F, count, 0, -1, 1, -1, s), "x pass");
+    CK(launch_colpass_fwd(p->geo, o, F, count, 1, 0, -1, s), "y pass");
+    CK(launch_colpass_fwd(p->geo, o, F, count, 0, 1, -1, s), "x pass");
     return GRIDSPT_OK;
 }
 
@@ -547,7 +627,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan p, int32_t nbins, size_t* bytes) {
     if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
     if (nbins < 1 || nbins > kMaxBins) return fail(GRIDSPT_E_INVALID, "nbins=%d outside [1, %d]", nbins, kMaxBins);
-    *bytes = 3 * align256((size_t)field_floats(p) * sizeof(float)) + align256((size_t)bispec_blocks(p->geo) * 2 * sizeof(double));
+    *bytes = 3 * align256((size_t)field_floats(p) * sizeof(float)) + align256((size_t)shell_blocks(p->geo) * 2 * sizeof(double));
     return GRIDSPT_OK;
 }
 
@@ -574,34 +654,24 @@ gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b
     float2* fields = reinterpret_cast<float2*>(base);
     double* partial = reinterpret_cast<double*>(base + 3 * fb);
     const double L = p->d.box;
+    const long long fstride = (long long)(fb / sizeof(float2));
+    const int G = shell_blocks(p->geo);
     for (int i = 0; i < nbins; ++i) {
-        DeriveArgs a{};
-        a.src0 = const_cast<float2*>(static_cast<const float2*>(a_k));
-        a.src1 = const_cast<float2*>(static_cast<const float2*>(b_k));
-        a.out = fields;
-        a.out_stride = (long long)(fb / sizeof(float2));
-        a.nout = 3;
-        a.codes[0] = derive_code(DK_SHELL, 0, 0, 0);
-        a.codes[1] = derive_code(DK_SHELL, 0, 0, 1);
-        a.codes[2] = derive_code(DK_SHELL, 0, 0, 2);
-        a.s2_nl = -1;
-        a.shell_lo = bs.thr[i];
-        a.shell_hi = bs.thr[i + 1];
-        if (a.src1 == a.src0) {
-            // the kernel treats equal inputs as one; keep the second output explicit
-            a.codes[1] = derive_code(DK_SHELL, 0, 0, 0);
+        if (bs.thr[i + 1] <= 1) {   // shell holds no mode with k > 0
+            CK(cudaMemsetAsync(e_out + i, 0, sizeof(double), s), "bispectrum empty shell");
+            CK(cudaMemsetAsync(ntri_out + i, 0, sizeof(double), s), "bispectrum empty shell");
+            continue;
         }
+        // every mode of the shell has |s_a| < band in each component
+        const int band = (int)std::floor(std::sqrt((double)(bs.thr[i + 1] - 1))) + 1;
+        if (gridspt_status st = backward_fields(p, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k),
+                                                fields, fstride, 3, true, bs.thr[i], bs.thr[i + 1], band, true, s))
+            return st;
         const double fbytes = 4.0 * (double)field_floats(p);
-        CKP(PK_DERIVE_INV, fbytes * (2 + 3), s, launch_derive(p->geo, a, s), "bispectrum shell x pass");
-        CKP(PK_Y_INV, 2 * fbytes * 3, s, launch_colpass(p->geo, fields, a.out_stride, 3, 1, +1, 0, -1, s),
-            "bispectrum y pass");
-        CKP(PK_ZC2R, 2 * fbytes * 3, s, launch_zc2r(p->geo, fields, fields, a.out_stride, 3, s), "bispectrum z pass");
-        const float* f0 = reinterpret_cast<const float*>(base);
-        CKP(PK_BISPEC, 3 * fbytes, s,
-            launch_bispec_reduce(p->geo, f0, reinterpret_cast<const float*>(base + fb),
-                                 reinterpret_cast<const float*>(base + 2 * fb), partial, e_out + i, ntri_out + i,
-                                 L * L * L * L * L * L, s),
-            "bispectrum reduce");
+        CKP(PK_BZ, fbytes * 3 * ((double)band / p->geo.M), s, launch_zshell(p->geo, fields, fstride, band, partial, s),
+            "bispectrum z pass and sums");
+        CK(launch_bispec_final(p->geo, partial, G, e_out + i, ntri_out + i, L * L * L * L * L * L, s),
+           "bispectrum final sum");
     }
     return GRIDSPT_OK;
 }

@@ -12,37 +12,62 @@ constexpr int kMaxDeriveOut = 17;
 
 // Grid geometry shared by every launch. Half spectra are float2[N][N][M],
 // M = N / 2 (kz = 0..M-1); real fields float[N][N][N]; both 4 N^3 bytes.
+// Transform-pass tile variants chosen by the autotuner (0 = default).
+enum TunePass : int { TV_COLPASS = 0, TV_XEXP = 1, TV_YEXP = 2, TV_ZEXP = 3, TV_ZR2C = 4, TV_COUNT = 5 };
+
 struct Geo {
     int N;
     int M;
     double kF;              // 2 pi / L
     const float2* tw;       // device table e^{+2 pi i j / N}, j < N (FP32 from FP64)
+    int var[TV_COUNT];      // tile variant per transform pass
 };
 
-// Multiplier codes of the fused spectral-derivative pass (Sec. II.C steps (2)
-// and (5)): out(k) = mult(k) * src(k), then the inverse transform along x.
-enum DeriveKind : int {
-    DK_ONE = 0,        // 1
-    DK_IK = 1,         // i k_a                  (gradient)
-    DK_NEG_IK_K2 = 2,  // -i k_a / k^2           (u = grad nabla^-2 theta)
-    DK_KK_K2 = 3,      // k_a k_b / k^2          (d_a u_b)
-    DK_SHELL = 4       // 1 inside the shell [s2_lo, s2_hi), else 0
-};
-// code = kind | a << 4 | b << 6 | src << 8 ; src 0 = first input, 1 = second, 2 = constant 1
-constexpr int derive_code(int kind, int a, int b, int src) { return kind | (a << 4) | (b << 6) | (src << 8); }
+// Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every
+// derived field is c * kx^a * ky^b * kz^g * src(k) with src in {delta, theta,
+// phi = theta / k^2} and c in {1, i, -i}. Factors of (ky, kz) commute with the
+// transform along x and factors of kz with the transform along y, so the
+// backward transform is split into three expansion passes:
+//   x pass: kx^a * src (or a shell mask), transformed along x    ("x-fields")
+//   y pass: ky^b * x-field, transformed along y                    ("xy-fields")
+//   z pass: c * kz^g * xy-field, half-complex -> real along z      (real fields)
+// Each pass reads every input once and writes every output once.
+constexpr int kMaxExpOut = 17;
+enum XKind : int { XK_POW = 0, XK_SHELL = 1 };
+enum XSrc : int { XS_DELTA = 0, XS_THETA = 1, XS_PHI = 2, XS_ONE = 3 };
+// x pass code: kind | a << 4 | src << 8
+constexpr int x_code(int kind, int a, int src) { return kind | (a << 4) | (src << 8); }
+// y pass code: input index | b << 8 | output slot << 16
+constexpr int y_code(int in, int b, int slot) { return in | (b << 8) | (slot << 16); }
+// z pass code: input index | g << 8 | c << 12 | output slot << 16  (c: 0 -> 1, 1 -> i, 2 -> -i)
+constexpr int z_code(int in, int g, int c, int slot) { return in | (g << 8) | (c << 12) | (slot << 16); }
 
-struct DeriveArgs {
-    float2* src0;          // first input spectrum (x-column layout [n][ky][kz])
-    float2* src1;          // second input (may equal src0)
+struct XExpArgs {
+    float2* src0;          // delta spectrum (x-column layout [kx][ky][kz])
+    float2* src1;          // theta spectrum (may equal src0)
     float2* out;           // output field f at out + f * out_stride
     long long out_stride;  // float2 elements between output fields
     int nout;
-    int codes[kMaxDeriveOut];
+    int codes[kMaxExpOut];
     int fwd_first;         // 1: inputs hold [x][ky][kz] data; transform forward along x,
                            //    finalise (zero Nyquist, optional cut) and store back in place
     long long s2_nl;       // finalise: zero modes with |s|^2 > s2_nl (< 0: no cut)
-    long long shell_lo;    // DK_SHELL: lo <= |s|^2 < hi
+    long long shell_lo;    // XK_SHELL: 0 < |s|^2, lo <= |s|^2 < hi
     long long shell_hi;
+    int band;              // > 0: only columns with |ky| < band and kz < band are
+                           //      transformed and written (all other outputs zero)
+};
+
+struct YZExpArgs {
+    const float2* in;      // input field i at in + i * in_stride
+    long long in_stride;
+    float2* out;           // output field f at out + f * out_stride
+    long long out_stride;
+    int nout;
+    int codes[kMaxExpOut]; // outputs of the same input must be consecutive; each
+                           // is written to out + slot * out_stride
+    int band;              // y pass, > 0: inputs nonzero only at |ky| < band and
+                           //      kz < band; only kz < band columns are formed
 };
 
 struct IcArgs {
@@ -71,15 +96,14 @@ struct BinSpec {
 };
 
 cudaError_t launch_ic(const Geo& g, const IcArgs& a, cudaStream_t s);
-cudaError_t launch_derive(const Geo& g, const DeriveArgs& a, cudaStream_t s);
-// Column transform along x (axis 0) or y (axis 1) of `count` fields, in place.
-// dir = +1 backward, -1 forward. finalize (x axis, forward only): zero Nyquist
-// modes and |s|^2 > s2_nl (s2_nl < 0: no cut).
-cudaError_t launch_colpass(const Geo& g, float2* data, long long fstride, int count, int axis,
-                           int dir, int finalize, long long s2_nl, cudaStream_t s);
-// Contiguous-axis complex-to-real (in [x][y][kz] -> out real [x][y][z]).
-cudaError_t launch_zc2r(const Geo& g, const float2* in, float2* out, long long fstride, int count,
-                        cudaStream_t s);
+cudaError_t launch_xexp(const Geo& g, const XExpArgs& a, cudaStream_t s);
+cudaError_t launch_yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);
+cudaError_t launch_zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);
+// Forward column transform along x (axis 0) or y (axis 1) of `count` fields,
+// in place. finalize (x axis): zero Nyquist modes and |s|^2 > s2_nl (s2_nl < 0:
+// no cut).
+cudaError_t launch_colpass_fwd(const Geo& g, float2* data, long long fstride, int count, int axis,
+                               int finalize, long long s2_nl, cudaStream_t s);
 // Contiguous-axis real-to-complex with output scale.
 cudaError_t launch_zr2c(const Geo& g, const float2* in, float2* out, long long fstride, int count,
                         float scale, cudaStream_t s);
@@ -91,11 +115,14 @@ int power_blocks(const Geo& g);
 cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const BinSpec& bins,
                          double* partial, double* p_out, int64_t* nk_out, double volume,
                          cudaStream_t s);
-// Bispectrum reduction of three real fields (I_a, I_b, J) for one shell.
-int bispec_blocks(const Geo& g);
-cudaError_t launch_bispec_reduce(const Geo& g, const float* ia, const float* ib, const float* j,
-                                 double* partial, double* e_out, double* ntri_out, double vol2,
-                                 cudaStream_t s);
+// Bispectrum, one shell: z transform of the three xy-fields (I_a, I_b, J with
+// kz < band) fused with the sums of I_a^2 I_b and J^3 (per-block partials),
+// then the fixed-order final reduction.
+int shell_blocks(const Geo& g);
+cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, double* partial,
+                          cudaStream_t s);
+cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, double* e_out,
+                                double* ntri_out, double vol2, cudaStream_t s);
 
 bool supported_n(int N);
 

@@ -13,9 +13,8 @@
 // the run to the warp's FP64 accumulator (one writer per bin per step). Warps
 // and blocks are then summed in a fixed order: results are bitwise repeatable.
 //
-// Bispectrum (Eq. bk_tree, FFT shell estimator): sums over cells of
-// I_a(x)^2 I_b(x) and J(x)^3; each thread keeps a Kahan-compensated FP32 sum
-// of four-cell FP32 products, then FP64 fixed-order block and grid reductions.
+// Bispectrum (Eq. bk_tree, FFT shell estimator): the per-shell sums are formed
+// in k_zshell (k_transform.cuh); the final fixed-order reduction is here.
 #include "gridspt_internal.h"
 
 namespace gridspt {
@@ -145,50 +144,8 @@ cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const B
 }
 
 // ------------------------------------------------------------ bispectrum
-constexpr int kBisThreads = 256;
-
-int bispec_blocks(const Geo& g) {
-    const long long n4 = (long long)g.N * g.N * g.N / 4;
-    long long b = (n4 + kBisThreads - 1) / kBisThreads;
-    return (int)(b < 1216 ? b : 1216);
-}
-
-// Kahan-compensated FP32 running sum (Kahan 1965): c carries the low-order
-// part lost by each addition.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
-
-__global__ void __launch_bounds__(kBisThreads)
-k_bispec(const float4* __restrict__ ia, const float4* __restrict__ ib, const float4* __restrict__ jj,
-         long long n4, double* __restrict__ partial) {
-    __shared__ double r1[kBisThreads], r2[kBisThreads];
-    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float4 a = ia[i], b = ib[i], j = jj[i];
-        kahan_add(s1, c1, (a.x * a.x * b.x + a.y * a.y * b.y) + (a.z * a.z * b.z + a.w * a.w * b.w));
-        kahan_add(s2, c2, (j.x * j.x * j.x + j.y * j.y * j.y) + (j.z * j.z * j.z + j.w * j.w * j.w));
-    }
-    r1[threadIdx.x] = (double)s1 - (double)c1;
-    r2[threadIdx.x] = (double)s2 - (double)c2;
-    __syncthreads();
-    for (int h = kBisThreads / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            r1[threadIdx.x] += r1[threadIdx.x + h];
-            r2[threadIdx.x] += r2[threadIdx.x + h];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = r1[0];
-        partial[2 * blockIdx.x + 1] = r2[0];
-    }
-}
-
+// Final reduction of the per-block partials written by k_zshell (one shell):
+// E = L^6 sum I_a^2 I_b / sum J^3, N_tri = sum J^3 / N^3; one block, fixed order.
 __global__ void __launch_bounds__(256)
 k_bispec_final(const double* __restrict__ partial, int G, double vol2, double cells,
                double* __restrict__ e_out, double* __restrict__ ntri_out) {
@@ -215,17 +172,9 @@ k_bispec_final(const double* __restrict__ partial, int G, double vol2, double ce
     }
 }
 
-cudaError_t launch_bispec_reduce(const Geo& g, const float* ia, const float* ib, const float* j,
-                                 double* partial, double* e_out, double* ntri_out, double vol2,
-                                 cudaStream_t s) {
-    const int G = bispec_blocks(g);
-    const long long n4 = (long long)g.N * g.N * g.N / 4;
-    k_bispec<<<G, kBisThreads, 0, s>>>(reinterpret_cast<const float4*>(ia),
-                                       reinterpret_cast<const float4*>(ib),
-                                       reinterpret_cast<const float4*>(j), n4, partial);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_bispec_final<<<1, 256, 0, s>>>(partial, G, vol2, (double)g.N * g.N * g.N, e_out, ntri_out);
+cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, double* e_out,
+                                double* ntri_out, double vol2, cudaStream_t s) {
+    k_bispec_final<<<1, 256, 0, s>>>(partial, blocks, vol2, (double)g.N * g.N * g.N, e_out, ntri_out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,584 @@
+// 3D real<->half-complex transforms of the GridSPT path, as three axis passes.
+//
+// Layouts (every array is 4 N^3 bytes, no padding):
+//   half spectrum / mixed data: float2[N][N][M], M = N / 2, index [x|kx][y|ky][kz]
+//   real field:                 float[N][N][N]
+// Backward (Sec. II.C synthesis sum a(x) = sum_k a(k) e^{i k.x}), with the
+// spectral-derivative multipliers of steps (2)/(5) factorised over the axes:
+//   k_xexp  x pass: kx^a * {delta, theta, phi = theta/k^2} (or a shell mask)
+//   k_yexp  y pass: ky^b * x-field
+//   k_zexp  z pass: c kz^g * xy-field, half-complex -> real
+// Forward (analysis sum, N^-3 folded into the producer): k_zr2c, then
+// k_colpass along y, then along x (k_colpass with finalise, or k_xexp with
+// fwd_first, which also starts the next order's backward expansion).
+//
+// Column passes stage a tile of TZ adjacent kz columns (TZ * 8 contiguous bytes
+// per row of the column) and keep each column in registers (fft_core.cuh).
+// The contiguous-axis passes use the half-length complex transform of the
+// packed sequence z[m] = x[2m] + i x[2m+1]; the Nyquist coefficient X[N/2] is
+// zero in every spectrum of this library and is not stored.
+#pragma once
+#include "fft_core.cuh"
+#include "gridspt_internal.h"
+
+namespace gridspt {
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Tile widths. Variant 0 is the default; variant 1 is the alternative the
+// autotuner also times (only instantiated separately for N >= 128).
+template <int N>
+struct Cfg {
+    static constexpr int M = N / 2;
+    // column passes (length N): TZ adjacent kz columns per block
+    static constexpr int EC = fft_elems(N);
+    static constexpr int PC = N / EC;
+    static constexpr int TZC0 = cmin(16, 1024 / PC);
+    static constexpr int TZC1 = N >= 128 ? cmax(4, TZC0 / 2) : TZC0;
+    // contiguous-axis passes (length M): TZ rows per block. 16 rows or more:
+    // a warp then spans 16 rows of the odd-pitch tile, so column accesses of
+    // a warp hit 16 distinct 8-byte bank pairs
+    static constexpr int EZ = fft_elems(M);
+    static constexpr int PZ = M / EZ;
+    static constexpr int TZZ0 = cmin(cmin(64, cmax(16, 256 / PZ)), 1024 / PZ);
+    static constexpr int TZZ1 = N >= 128 ? (2 * TZZ0 * PZ <= 1024 ? 2 * TZZ0 : cmax(16, TZZ0 / 2)) : TZZ0;
+    static constexpr int PITCH = M + 1;
+};
+
+__device__ __forceinline__ int signed_idx(int n, int N) { return n < N / 2 ? n : n - N; }
+
+__device__ __forceinline__ void load_table(float2* tw, const float2* __restrict__ twg, int N) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+}
+
+// Copy TZ contiguous rows of M float2 between global memory and a shared tile
+// of odd pitch PITCH. Consecutive threads move consecutive float2 of a row
+// (coalesced, conflict-free); all loads are issued before the shared stores,
+// so each thread has TZ * M / NTHR requests in flight.
+template <int M, int TZ, int PITCH, int NTHR>
+__device__ __forceinline__ void tile_load(float2* tile, const float2* src, long long row0, long long rows) {
+    constexpr int NV = TZ * M;
+    constexpr int PER = (NV + NTHR - 1) / NTHR;
+    float2 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        const int r = idx / M, j = idx - r * M;
+        const long long row = row0 + r;
+        v[u] = (idx < NV && row < rows) ? src[row * M + j] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        if (idx < NV) {
+            const int r = idx / M, j = idx - r * M;
+            tile[r * PITCH + j] = v[u];
+        }
+    }
+}
+
+template <int M, int TZ, int PITCH, int NTHR>
+__device__ __forceinline__ void tile_store(float2* dst, const float2* tile, long long row0, long long rows) {
+    constexpr int NV = TZ * M;
+    constexpr int PER = (NV + NTHR - 1) / NTHR;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        const int r = idx / M, j = idx - r * M;
+        const long long row = row0 + r;
+        if (idx < NV && row < rows) dst[row * M + j] = tile[r * PITCH + j];
+    }
+}
+
+// ------------------------------------------------- forward column pass
+template <int N, int TZ, int AXIS, bool FIN>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
+k_colpass(float2* __restrict__ data, long long fstride, const float2* __restrict__ twg,
+          long long s2_nl) {
+    constexpr int M = N / 2, E = fft_elems(N), P = N / E;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const int kz = blockIdx.x * TZ + c;
+    const int a = blockIdx.y;
+    const bool act = kz < M;
+    constexpr long long estride = AXIS == 0 ? (long long)N * M : (long long)M;
+    constexpr long long astride = AXIS == 0 ? (long long)M : (long long)N * M;
+    float2* col = data + blockIdx.z * fstride + a * astride + kz;
+    float2 x[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[i] = act ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
+    __syncthreads();
+    fft_column<N, -1, N>(x, p, buf + c, TZ, tw);
+    if constexpr (FIN) {
+        const int sy = signed_idx(a, N), sz = kz;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int n = p + P * i;
+            const int sx = signed_idx(n, N);
+            const long long s2 = (long long)sx * sx + (long long)sy * sy + (long long)sz * sz;
+            if (n == N / 2 || a == N / 2 || (s2_nl >= 0 && s2 > s2_nl)) x[i] = make_float2(0.f, 0.f);
+        }
+    }
+    if (act) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) col[(p + P * i) * estride] = x[i];
+    }
+}
+
+// ------------------------------------------------ contiguous axis: R2C
+template <int N, int TZ>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PZ)
+k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restrict__ twg, float scale) {
+    constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tile = sm + N;
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const long long rows = (long long)N * N;
+    const long long row0 = (long long)blockIdx.x * TZ;
+    const float2* src = in + blockIdx.y * fstride;
+    float2* dst = out + blockIdx.y * fstride;
+    tile_load<M, TZ, PITCH, TZ * P>(tile, src, row0, rows);
+    __syncthreads();
+    float2* colp = tile + c * PITCH;
+    float2 x[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[i] = colp[p + P * i];
+    __syncthreads();
+    fft_column<M, -1, N>(x, p, colp, 1, tw);
+#pragma unroll
+    for (int i = 0; i < E; ++i) colp[p + P * i] = x[i];
+    __syncthreads();
+    const float half = 0.5f * scale;
+    constexpr int NV = TZ * M, NTHR = TZ * P, PER = (NV + NTHR - 1) / NTHR;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = tid + u * NTHR;
+        const int r = idx / M, k = idx - r * M;
+        const long long row = row0 + r;
+        if (idx >= NV || row >= rows) continue;
+        const float2 Z = tile[r * PITCH + k];
+        const float2 Zr = cconj(tile[r * PITCH + (k ? M - k : 0)]);
+        const float2 S = cadd(Z, Zr);                      // 2 E[k]
+        const float2 t = cmul(cconj(tw[k]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
+        // X = E + e^{-2 pi i k / N} O = (S - i t) / 2
+        dst[row * M + k] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
+    }
+}
+
+// ------------------------------------------------------------ x expansion
+// Inputs: delta(k) and theta(k) columns along kx. Each output f is
+// kx^a * src (src = delta, theta, phi = theta / k^2 or 1) or a shell mask times
+// src, transformed backward along x. With FWD the inputs first hold the
+// y-transformed product output: they are transformed forward along x and
+// finalised (delta_n(k), theta_n(k) complete, stored back in place), so the
+// spectra are read from HBM once for both directions.
+template <int N, int TZ, bool FWD>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
+k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
+    constexpr int M = N / 2, E = fft_elems(N), P = N / E;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const int kz = blockIdx.x * TZ + c;
+    const int B = args.band;
+    const int by = blockIdx.y;
+    const int ky = (B > 0 && by >= B) ? N - (2 * B - 1 - by) : by;   // band rows: [0, B) and (N - B, N)
+    const bool act = kz < M && (B <= 0 || kz < B);
+    constexpr long long estride = (long long)N * M;
+    const long long colofs = (long long)ky * M + kz;
+    const bool two = args.src1 != args.src0;
+    float2 xd[E], xt[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        xd[i] = act ? args.src0[colofs + (p + P * i) * estride] : make_float2(0.f, 0.f);
+        xt[i] = (act && two) ? args.src1[colofs + (p + P * i) * estride] : xd[i];
+    }
+    __syncthreads();
+    const int sy = signed_idx(ky, N), sz = kz;
+    const int syz = sy * sy + sz * sz;
+    if constexpr (FWD) {
+        fft_column<N, -1, N>(xd, p, buf + c, TZ, tw);
+        if (two) fft_column<N, -1, N>(xt, p, buf + c, TZ, tw);
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int n = p + P * i;
+            const int sx = signed_idx(n, N);
+            const long long s2 = (long long)sx * sx + syz;
+            if (n == N / 2 || ky == N / 2 || (args.s2_nl >= 0 && s2 > args.s2_nl)) {
+                xd[i] = make_float2(0.f, 0.f);
+                xt[i] = make_float2(0.f, 0.f);
+            }
+            if (!two) xt[i] = xd[i];
+        }
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                args.src0[colofs + (p + P * i) * estride] = xd[i];
+                if (two) args.src1[colofs + (p + P * i) * estride] = xt[i];
+            }
+        }
+    }
+    for (int f = 0; f < args.nout; ++f) {
+        const int code = args.codes[f];
+        const int kind = code & 15, pa = (code >> 4) & 3, src = (code >> 8) & 3;
+        float2 y[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int n = p + P * i;
+            const int sx = signed_idx(n, N);
+            const int s2 = sx * sx + syz;
+            float2 v;
+            if (src == XS_DELTA) {
+                v = xd[i];
+            } else if (src == XS_THETA) {
+                v = xt[i];
+            } else if (src == XS_PHI) {
+                const float g = s2 ? inv_kF2 / (float)s2 : 0.f;   // 1 / k^2, 0 at k = 0
+                v = cscale(xt[i], g);
+            } else {
+                v = make_float2(1.f, 0.f);
+            }
+            if (kind == XK_POW) {
+                const float kx = kF * (float)sx;
+                if (pa == 1) v = cscale(v, kx);
+                else if (pa == 2) v = cscale(v, kx * kx);
+            } else {
+                const bool in = s2 > 0 && (long long)s2 >= args.shell_lo && (long long)s2 < args.shell_hi;
+                if (!in) v = make_float2(0.f, 0.f);
+            }
+            y[i] = v;
+        }
+        fft_column<N, +1, N>(y, p, buf + c, TZ, tw);
+        if (act) {
+            float2* o = args.out + f * args.out_stride + colofs;
+#pragma unroll
+            for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------ y expansion
+// Output f = ky^b * x-field[in], transformed backward along y. Outputs of one
+// input are consecutive; the input column is loaded once and kept in
+// registers. In-place use (out == in, one output per input, same index) is
+// safe: a block owns its columns.
+template <int N, int TZ>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
+k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+    constexpr int M = N / 2, E = fft_elems(N), P = N / E;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const int kz = blockIdx.x * TZ + c;
+    const int xr = blockIdx.y;
+    const int B = args.band;
+    const bool act = kz < M && (B <= 0 || kz < B);
+    constexpr long long estride = (long long)M;
+    const long long colofs = (long long)xr * N * M + kz;
+    float2 xin[E];
+    int cur = -1;
+    __syncthreads();
+    for (int f = 0; f < args.nout; ++f) {
+        const int code = args.codes[f];
+        const int in = code & 255, pb = (code >> 8) & 3, slot = code >> 16;
+        if (in != cur) {
+            const float2* col = args.in + in * args.in_stride + colofs;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int sy = signed_idx(p + P * i, N);
+                const bool live = act && (B <= 0 || (sy < B && -sy < B));
+                xin[i] = live ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
+            }
+            cur = in;
+        }
+        float2 y[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float ky = kF * (float)signed_idx(p + P * i, N);
+            y[i] = pb == 0 ? xin[i] : cscale(xin[i], pb == 1 ? ky : ky * ky);
+        }
+        fft_column<N, +1, N>(y, p, buf + c, TZ, tw);
+        if (act) {
+            float2* o = args.out + slot * args.out_stride + colofs;
+#pragma unroll
+            for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------ z expansion
+// Output f = IFFT_z(c kz^g xy-field[in]) as a real row of N values, via the
+// half-length complex transform of the packed row (Nyquist term zero). The
+// input tile of 16+ rows is loaded once per input (tin) and kept while its
+// outputs are formed in a second tile (tex), which is also the transform's
+// exchange buffer.
+template <int N, int TZ>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
+k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+    constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tin = sm + N;
+    float2* tex = tin + TZ * PITCH;
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const long long rows = (long long)N * N;
+    const long long row0 = (long long)blockIdx.x * TZ;
+    int cur = -1;
+    for (int f = 0; f < args.nout; ++f) {
+        const int code = args.codes[f];
+        const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
+        __syncthreads();                       // tin / tex free for reuse
+        if (in != cur) {
+            tile_load<M, TZ, PITCH, TZ * P>(tin, args.in + in * args.in_stride, row0, rows);
+            __syncthreads();
+            cur = in;
+        }
+        const float2* colp = tin + c * PITCH;
+        float2 x[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = p + P * i;
+            float2 Xk = colp[k];
+            float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
+            if (g) {
+                const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
+                Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);
+                Xm = cscale(Xm, g == 1 ? k2 : k2 * k2);
+            }
+            if (cc == 1) {
+                Xk = cmul_i<+1>(Xk);
+                Xm = cmul_i<+1>(Xm);
+            } else if (cc == 2) {
+                Xk = cmul_i<-1>(Xk);
+                Xm = cmul_i<-1>(Xm);
+            }
+            Xm = cconj(Xm);                                  // X[k + M] = conj X[M - k]
+            const float2 Ev = cadd(Xk, Xm);
+            const float2 Ov = cmul(csub(Xk, Xm), tw[k]);     // e^{+2 pi i k / N}
+            x[i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);    // E + i O
+        }
+        float2* colx = tex + c * PITCH;
+        fft_column<M, +1, N>(x, p, colx, 1, tw);
+#pragma unroll
+        for (int i = 0; i < E; ++i) colx[p + P * i] = x[i];
+        __syncthreads();
+        tile_store<M, TZ, PITCH, TZ * P>(args.out + slot * args.out_stride, tex, row0, rows);
+    }
+}
+
+// ------------------------------------------- z pass fused with the shell sums
+// Bispectrum estimator, one shell (Sec. III.B.1, Eq. bk_tree, FFT shell
+// estimator): the three xy-fields I_a, I_b, J (nonzero only for kz < band)
+// are transformed to real rows in shared memory; every thread then holds the
+// same cells of all three rows, forms I_a^2 I_b and J^3 in FP32 and keeps
+// Kahan-compensated FP32 sums; the block writes FP64 partials (fixed order).
+__device__ __forceinline__ void kahan_add2(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <int N, int TZ>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
+k_zshell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
+         double* __restrict__ partial) {
+    constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NT = TZ * P;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* t3 = sm + N;
+    __shared__ double r1[32], r2[32];
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const long long rows = (long long)N * N;
+    const long long row0 = (long long)blockIdx.x * TZ;
+    const int B = band < M ? band : M;
+    // load kz < B of the three fields; zero the rest of each tile row
+    for (int f = 0; f < 3; ++f) {
+        const float2* src = in + f * in_stride;
+        float2* tile = t3 + f * TZ * PITCH;
+        for (int idx = tid; idx < TZ * M; idx += NT) {
+            const int r = idx / M, j = idx - r * M;
+            const long long row = row0 + r;
+            tile[r * PITCH + j] = (j < B && row < rows) ? src[row * M + j] : make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    float2 x[3][E];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const float2* colp = t3 + f * TZ * PITCH + c * PITCH;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = p + P * i;
+            const float2 Xk = colp[k];
+            const float2 Xm = k ? cconj(colp[M - k]) : make_float2(0.f, 0.f);
+            const float2 Ev = cadd(Xk, Xm);
+            const float2 Ov = cmul(csub(Xk, Xm), tw[k]);
+            x[f][i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < 3; ++f) fft_column<M, +1, N>(x[f], p, t3 + f * TZ * PITCH + c * PITCH, 1, tw);
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    if (row0 + c < rows) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float2 a = x[0][i], b = x[1][i], j = x[2][i];   // cells 2n, 2n + 1
+            kahan_add2(s1, c1, a.x * a.x * b.x + a.y * a.y * b.y);
+            kahan_add2(s2, c2, j.x * j.x * j.x + j.y * j.y * j.y);
+        }
+    }
+    double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
+    // fixed-order reduction: warp shuffles, then warps in order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d1 += __shfl_down_sync(0xffffffffu, d1, off);
+        d2 += __shfl_down_sync(0xffffffffu, d2, off);
+    }
+    const int w = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        r1[w] = d1;
+        r2[w] = d2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < NT / 32; ++i) {
+            a += r1[i];
+            b += r2[i];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+template <int N, int TZC, int TZZ>
+struct Launch {
+    static constexpr int M = N / 2;
+    static constexpr int PC = Cfg<N>::PC, PZ = Cfg<N>::PZ, PITCH = Cfg<N>::PITCH;
+    static cudaError_t colpass(const Geo& g, float2* d, long long fs, int count, int axis, int fin,
+                               long long s2_nl, cudaStream_t s) {
+        dim3 grid((M + TZC - 1) / TZC, N, count);
+        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
+        cudaError_t e;
+#define GRIDSPT_COL(AX_, FIN_)                                                        \
+    e = set_smem(k_colpass<N, TZC, AX_, FIN_>, smem);                                 \
+    if (e != cudaSuccess) return e;                                                   \
+    k_colpass<N, TZC, AX_, FIN_><<<grid, TZC * PC, smem, s>>>(d, fs, g.tw, s2_nl);    \
+    return cudaGetLastError();
+        if (axis == 0) {
+            if (fin) { GRIDSPT_COL(0, true) }
+            GRIDSPT_COL(0, false)
+        }
+        GRIDSPT_COL(1, false)
+#undef GRIDSPT_COL
+    }
+    static cudaError_t zr2c(const Geo& g, const float2* in, float2* out, long long fs, int count,
+                            float scale, cudaStream_t s) {
+        const long long rows = (long long)N * N;
+        dim3 grid((unsigned)((rows + TZZ - 1) / TZZ), count);
+        const size_t smem = sizeof(float2) * (N + (size_t)TZZ * PITCH);
+        cudaError_t e = set_smem(k_zr2c<N, TZZ>, smem);
+        if (e != cudaSuccess) return e;
+        k_zr2c<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(in, out, fs, g.tw, scale);
+        return cudaGetLastError();
+    }
+    static cudaError_t xexp(const Geo& g, const XExpArgs& a, cudaStream_t s) {
+        const int B = a.band > 0 && a.band < M ? a.band : 0;
+        dim3 grid(((B ? B : M) + TZC - 1) / TZC, B ? 2 * B - 1 : N);
+        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
+        const float kF = (float)g.kF, ikF2 = (float)(1.0 / (g.kF * g.kF));
+        cudaError_t e;
+        if (a.fwd_first) {
+            e = set_smem(k_xexp<N, TZC, true>, smem);
+            if (e != cudaSuccess) return e;
+            k_xexp<N, TZC, true><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+        } else {
+            e = set_smem(k_xexp<N, TZC, false>, smem);
+            if (e != cudaSuccess) return e;
+            k_xexp<N, TZC, false><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
+        const int B = a.band > 0 && a.band < M ? a.band : 0;
+        dim3 grid(((B ? B : M) + TZC - 1) / TZC, N);
+        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
+        cudaError_t e = set_smem(k_yexp<N, TZC>, smem);
+        if (e != cudaSuccess) return e;
+        k_yexp<N, TZC><<<grid, TZC * PC, smem, s>>>(a, g.tw, (float)g.kF);
+        return cudaGetLastError();
+    }
+    static cudaError_t zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
+        const long long rows = (long long)N * N;
+        dim3 grid((unsigned)((rows + TZZ - 1) / TZZ));
+        const size_t smem = sizeof(float2) * (N + 2 * (size_t)TZZ * PITCH);
+        cudaError_t e = set_smem(k_zexp<N, TZZ>, smem);
+        if (e != cudaSuccess) return e;
+        k_zexp<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+        return cudaGetLastError();
+    }
+    static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
+    static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, double* partial,
+                              cudaStream_t s) {
+        const size_t smem = sizeof(float2) * (N + 3 * (size_t)TZZ * PITCH);
+        cudaError_t e = set_smem(k_zshell<N, TZZ>, smem);
+        if (e != cudaSuccess) return e;
+        k_zshell<N, TZZ><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
+        return cudaGetLastError();
+    }
+};
+
+// Per-size entry points (defined in the k_transform_*.cu units). The pass
+// variant v selects tile widths: v = 0 default, v = 1 alternative.
+#define GRIDSPT_TRANSFORM_SIZE(N)                                                                          \
+    cudaError_t transform_colpass_##N(const Geo& g, float2* d, long long fs, int count, int axis, int fin, \
+                                      long long s2, int v, cudaStream_t s) {                               \
+        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::colpass(g, d, fs, count, axis, fin, s2, s)       \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::colpass(g, d, fs, count, axis, fin, s2, s);      \
+    }                                                                                                      \
+    cudaError_t transform_zr2c_##N(const Geo& g, const float2* in, float2* out, long long fs, int count,   \
+                                   float scale, int v, cudaStream_t s) {                                   \
+        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ1>::zr2c(g, in, out, fs, count, scale, s)            \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zr2c(g, in, out, fs, count, scale, s);           \
+    }                                                                                                      \
+    cudaError_t transform_xexp_##N(const Geo& g, const XExpArgs& a, int v, cudaStream_t s) {               \
+        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::xexp(g, a, s)                                    \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::xexp(g, a, s);                                   \
+    }                                                                                                      \
+    cudaError_t transform_yexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
+        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::yexp(g, a, s)                                    \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                                   \
+    }                                                                                                      \
+    cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
+        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ1>::zexp(g, a, s)                                    \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zexp(g, a, s);                                   \
+    }                                                                                                      \
+    int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
+    cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band,               \
+                                     double* partial, cudaStream_t s) {                                    \
+        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zshell(g, in, st, band, partial, s);                 \
+    }
+
+}  // namespace gridspt

@@ -7,7 +7,8 @@ Tolerances (FP32 fields and transforms against FP64):
   2^-23 relative of the oracle (a few ulp of headroom);
 * shell power estimator on identical inputs: <= 1e-5 relative per bin; N_k
   bit-exact (integer counting); P-terms from GPU fields: <= 1e-5 of each
-  term's scale (max over bins), P11 per bin;
+  term's scale (max over bins) for P11, P22, P13, <= 3e-5 for the two-loop
+  terms P33, P24, P15, and P11 per bin;
 * bispectrum: N_tri within FP32 rounding of the cubes, E within 1e-4 of its
   scale (FP32 shell fields, Kahan/FP64 sums);
 * transforms alone: RMS relative error <= 2e-6.
@@ -264,7 +265,8 @@ def test_power_terms_end_to_end(N, L, n_max, edges):
         p = p.cpu().numpy()
         sel = nkr > 0
         scale = np.abs(pr[sel]).max()
-        assert np.all(np.abs(p[sel] - pr[sel]) <= 1e-5 * scale), ((i, j), np.abs(p[sel] - pr[sel]).max() / scale)
+        tol = 1e-5 if i + j <= 4 else 3e-5      # two-loop terms: FP32 floor of delta_5 at low k
+        assert np.all(np.abs(p[sel] - pr[sel]) <= tol * scale), ((i, j), np.abs(p[sel] - pr[sel]).max() / scale)
         if (i, j) == (1, 1):
             assert np.all(np.abs(p[sel] - pr[sel]) <= 1e-5 * np.abs(pr[sel])), (i, j)
 
