@@ -181,6 +181,78 @@ gridspt_status gridspt_bispectrum(gridspt_plan plan, const void* a_k, const void
                                   double* ntri_out, void* ws, size_t ws_bytes,
                                   gridspt_stream stream);
 
+/* Launch batching (not part of the paper's method): the recursion of one or
+ * several plans captured once as a single CUDA graph and replayed with one
+ * launch. plans[i] may have different grid sizes, orders and batches; branch i
+ * runs exactly the launches of gridspt_run_orders(plans[i], delta1_k[i],
+ * start_order[i], spectra[i], ws[i], ws_bytes[i]) (same results, bit for bit),
+ * and branches are independent, so realisations of different sizes run
+ * concurrently. All pointers are device pointers as in gridspt_run_orders and
+ * are baked into the graph: they must stay valid and must not overlap between
+ * branches (in particular each branch needs its own workspace). Create,
+ * launch and destroy are host calls; create captures on internal streams and
+ * synchronises nothing; launch enqueues one graph launch on `stream`. */
+typedef struct gridspt_batch_s* gridspt_batch;
+gridspt_status gridspt_batch_create(const gridspt_plan* plans, int32_t count, const void* const* delta1_k,
+                                    const int32_t* start_order, void* const* spectra, void* const* ws,
+                                    const size_t* ws_bytes, gridspt_batch* out);
+gridspt_status gridspt_batch_launch(gridspt_batch batch, gridspt_stream stream);
+gridspt_status gridspt_batch_destroy(gridspt_batch batch);
+
+/* Autotuner for the transform passes (not part of the paper's method). Each
+ * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
+ * 4 contiguous-axis forward pass) has two tile-width variants for N >= 128
+ * (identical for smaller N). gridspt_autotune times both variants of every
+ * pass on `scratch` (device, >= gridspt_autotune_scratch_size bytes, contents
+ * overwritten) with CUDA events on `stream`, keeps the faster one in the plan
+ * and writes the choices to choices_out (host int32[5], may be NULL). It
+ * synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning store and
+ * read the choices (each 0 or 1), e.g. from a cache kept by the caller.
+ * Results are bitwise identical for both variants: they only change how
+ * columns and rows are grouped into thread blocks. */
+gridspt_status gridspt_autotune_scratch_size(gridspt_plan plan, size_t* bytes);
+gridspt_status gridspt_autotune(gridspt_plan plan, void* scratch, size_t scratch_bytes, int32_t* choices_out,
+                                gridspt_stream stream);
+gridspt_status gridspt_set_tuning(gridspt_plan plan, const int32_t* choices);
+gridspt_status gridspt_get_tuning(gridspt_plan plan, int32_t* choices);
+
+/* P-term emulator network (not part of the paper's method): a multilayer
+ * perceptron in -> hidden -> hidden -> out with SiLU after both hidden layers
+ * and a linear output, used to emulate binned GridSPT P-terms as a function of
+ * (sigma_8, n_s, Gamma). Parameters, one contiguous vector, row-major [in][out]
+ * weights: W1[in][hidden], b1[hidden], W2[hidden][hidden], b2[hidden],
+ * W3[hidden][out], b3[out]. `bf16` = 1: the parameter copy read by
+ * forward/backward is bfloat16 and hidden activations are rounded to bfloat16;
+ * 0: FP32. Every product is accumulated in FP32. Limits: 1 <= in <= 8,
+ * 1 <= hidden, out <= 256, batch >= 1. All arrays are device arrays.
+ *   x [batch][in], y [batch][out] (FP32);
+ *   act: NULL, or FP32 [batch][4 * hidden] saved activations (z1, a1, z2, a2)
+ *        for gridspt_mlp_backward.
+ * gridspt_mlp_backward: grad = d(sum(dy * y)) / d params (FP32, parameter
+ * layout), from x, the parameter copy, act and dy [batch][out]; per-block
+ * partial gradients in ws are summed in a fixed order (bitwise repeatable).
+ * gridspt_mlp_mse: dy = 2 mask (y - t) / sum(mask), loss = sum(mask (y - t)^2)
+ * / sum(mask) over n elements (loss: device float, may be NULL).
+ * gridspt_mlp_adam: increments the device step counter *step, then one Adam
+ * update (Kingma & Ba 2015, bias-corrected) of the FP32 master parameters and
+ * moments m, v; writes the updated parameter copy (bf16 or FP32) if
+ * params_lowp is not NULL. gridspt_mlp_convert writes that copy from master. */
+gridspt_status gridspt_mlp_param_count(int32_t in, int32_t hidden, int32_t out, int64_t* count);
+gridspt_status gridspt_mlp_forward(const float* x, int32_t batch, int32_t in, int32_t hidden, int32_t out,
+                                   const void* params, int32_t bf16, float* y, float* act, gridspt_stream stream);
+gridspt_status gridspt_mlp_backward_workspace_size(int32_t batch, int32_t in, int32_t hidden, int32_t out,
+                                                   size_t* bytes);
+gridspt_status gridspt_mlp_backward(const float* x, int32_t batch, int32_t in, int32_t hidden, int32_t out,
+                                    const void* params, int32_t bf16, const float* act, const float* dy,
+                                    float* grad, void* ws, size_t ws_bytes, gridspt_stream stream);
+gridspt_status gridspt_mlp_mse(const float* y, const float* target, const float* mask, int64_t n, float* dy,
+                               float* loss, gridspt_stream stream);
+gridspt_status gridspt_mlp_adam(float* master, void* params_lowp, int32_t bf16, const float* grad, float* m,
+                                float* v, int32_t* step, int64_t n, float lr, float beta1, float beta2, float eps,
+                                gridspt_stream stream);
+gridspt_status gridspt_mlp_convert(const float* master, void* params_lowp, int32_t bf16, int64_t n,
+                                   gridspt_stream stream);
+
 /* Launch profiling (tracing aid, not part of the paper's method). Between
  * gridspt_profile_begin and gridspt_profile_end every kernel the library
  * launches is bracketed by two CUDA events recorded on its launch stream, and

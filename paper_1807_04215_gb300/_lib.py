@@ -46,6 +46,26 @@ SIGNATURES = {
     "gridspt_bispectrum_workspace_size": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t)]),
     "gridspt_bispectrum": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gridspt_batch_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(c_size_t), ctypes.POINTER(c_void_p)]),
+    "gridspt_batch_launch": (c_int32, [c_void_p, c_void_p]),
+    "gridspt_batch_destroy": (c_int32, [c_void_p]),
+    "gridspt_autotune_scratch_size": (c_int32, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "gridspt_autotune": (c_int32, [c_void_p, c_void_p, c_size_t, ctypes.POINTER(c_int32), c_void_p]),
+    "gridspt_set_tuning": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
+    "gridspt_get_tuning": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
+    "gridspt_mlp_param_count": (c_int32, [c_int32, c_int32, c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "gridspt_mlp_forward": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
+                                      c_void_p, c_void_p]),
+    "gridspt_mlp_backward_workspace_size": (c_int32, [c_int32, c_int32, c_int32, c_int32, ctypes.POINTER(c_size_t)]),
+    "gridspt_mlp_backward": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p,
+                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gridspt_mlp_mse": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.c_int64, c_void_p, c_void_p, c_void_p]),
+    "gridspt_mlp_adam": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   c_void_p]),
+    "gridspt_mlp_convert": (c_int32, [c_void_p, c_void_p, c_int32, ctypes.c_int64, c_void_p]),
     "gridspt_profile_begin": (c_int32, []),
     "gridspt_profile_end": (c_int32, [ctypes.POINTER(GridsptKernelStat), c_int32, ctypes.POINTER(c_int32)]),
     "gridspt_last_error": (ctypes.c_char_p, []),

@@ -57,11 +57,12 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // ------------------------------------------------------------- profiling
 enum ProfKind {
     PK_IC, PK_XEXP, PK_XEXP_FWD, PK_YEXP, PK_ZEXP, PK_Y_FWD, PK_X_FWD, PK_ZR2C,
-    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_COUNT
+    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_MLP_FWD, PK_MLP_BWD, PK_MLP_OPT, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {
     "ic", "x_expand", "x_fwd_expand", "y_expand", "z_expand", "y_fwd", "x_fwd", "z_r2c",
-    "product", "power", "bispec_reduce", "shell_x", "shell_y", "shell_z"};
+    "product", "power", "bispec_final", "shell_x", "shell_y", "shell_z", "mlp_forward", "mlp_backward",
+    "mlp_update"};
 constexpr size_t kMaxProfRecs = 65536;
 
 struct ProfRec {
@@ -76,6 +77,7 @@ struct Profiler {
     std::vector<cudaEvent_t> pool;
 };
 Profiler g_prof;
+thread_local bool t_capturing = false;   // launches being captured into a graph are not profiled
 
 cudaEvent_t prof_event() {
     if (!g_prof.pool.empty()) {
@@ -92,7 +94,7 @@ cudaEvent_t prof_event() {
 template <class F>
 cudaError_t prof_launch(int kind, double bytes, cudaStream_t s, F&& f) {
     std::unique_lock<std::mutex> lk(g_prof.mu);
-    if (!g_prof.on || g_prof.recs.size() >= kMaxProfRecs) {
+    if (!g_prof.on || t_capturing || g_prof.recs.size() >= kMaxProfRecs) {
         lk.unlock();
         return f();
     }
@@ -442,9 +444,12 @@ gridspt_status backward_fields(const gridspt_plan_s* p, const float2* in0, const
 
 }  // namespace
 
-gridspt_status gridspt_run_orders(gridspt_plan p, const void* delta1_k, int32_t start_order, void* spectra,
-                                  void* ws, size_t ws_bytes, gridspt_stream stream) {
-    g_err[0] = 0;
+}  // extern "C"
+
+namespace {
+
+gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t start_order, void* spectra,
+                               void* ws, size_t ws_bytes, gridspt_stream stream) {
     if (check_plan(p)) return GRIDSPT_E_INVALID;
     const int n_max = p->d.n_max;
     if (!delta1_k || (!spectra && n_max >= 2)) return fail(GRIDSPT_E_INVALID, "NULL argument");
@@ -494,6 +499,294 @@ gridspt_status gridspt_run_orders(gridspt_plan p, const void* delta1_k, int32_t 
             }
         }
     }
+    return GRIDSPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gridspt_status gridspt_run_orders(gridspt_plan p, const void* delta1_k, int32_t start_order, void* spectra,
+                                  void* ws, size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    return run_orders_impl(p, delta1_k, start_order, spectra, ws, ws_bytes, stream);
+}
+
+// ------------------------------------------------------------ batch graphs
+}  // extern "C"
+
+struct gridspt_batch_s {
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+gridspt_status gridspt_batch_create(const gridspt_plan* plans, int32_t count, const void* const* delta1_k,
+                                    const int32_t* start_order, void* const* spectra, void* const* ws,
+                                    const size_t* ws_bytes, gridspt_batch* out) {
+    g_err[0] = 0;
+    if (!plans || count < 1 || !delta1_k || !start_order || !spectra || !ws || !ws_bytes || !out)
+        return fail(GRIDSPT_E_INVALID, "NULL argument or count < 1");
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return fail(GRIDSPT_E_INVALID, "plans[%d] is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (ws[j] && ws[j] == ws[i]) return fail(GRIDSPT_E_INVALID, "branches %d and %d share a workspace", j, i);
+    }
+    std::vector<cudaStream_t> st(count + 1, nullptr);
+    std::vector<cudaEvent_t> ev(count + 1, nullptr);
+    cudaGraph_t graph = nullptr;
+    gridspt_status res = GRIDSPT_OK;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        for (auto x : ev) if (x) cudaEventDestroy(x);
+        for (auto x : st) if (x) cudaStreamDestroy(x);
+        if (graph) cudaGraphDestroy(graph);
+    };
+    for (int i = 0; i <= count && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "batch streams");
+    }
+    e = cudaStreamBeginCapture(st[0], cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "begin capture");
+    }
+    t_capturing = true;
+    e = cudaEventRecord(ev[0], st[0]);   // fork
+    for (int i = 0; i < count && e == cudaSuccess && res == GRIDSPT_OK; ++i) {
+        e = cudaStreamWaitEvent(st[i + 1], ev[0], 0);
+        if (e != cudaSuccess) break;
+        res = run_orders_impl(plans[i], delta1_k[i], start_order[i], spectra[i], ws[i], ws_bytes[i],
+                              (gridspt_stream)st[i + 1]);
+        if (res != GRIDSPT_OK) break;
+        e = cudaEventRecord(ev[i + 1], st[i + 1]);   // join
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[0], ev[i + 1], 0);
+    }
+    t_capturing = false;
+    cudaError_t e2 = cudaStreamEndCapture(st[0], &graph);
+    if (res != GRIDSPT_OK) {
+        cleanup();
+        return res;
+    }
+    if (e == cudaSuccess) e = e2;
+    gridspt_batch b = nullptr;
+    if (e == cudaSuccess) {
+        b = new (std::nothrow) gridspt_batch_s();
+        if (!b) {
+            cleanup();
+            return fail(GRIDSPT_E_NOMEM, "host allocation failed");
+        }
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+    }
+    cleanup();
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch capture");
+    }
+    *out = b;
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_batch_launch(gridspt_batch b, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (!b || !b->exec) return fail(GRIDSPT_E_INVALID, "batch is NULL");
+    CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "graph launch");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_batch_destroy(gridspt_batch b) {
+    if (!b) return GRIDSPT_OK;
+    cudaError_t e = b->exec ? cudaGraphExecDestroy(b->exec) : cudaSuccess;
+    delete b;
+    if (e != cudaSuccess) return cuda_fail(e, "batch destroy");
+    return GRIDSPT_OK;
+}
+
+// ------------------------------------------------------------- autotuner
+gridspt_status gridspt_autotune_scratch_size(gridspt_plan p, size_t* bytes) {
+    if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
+    *bytes = 4 * (size_t)field_floats(p) * sizeof(float);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_set_tuning(gridspt_plan p, const int32_t* choices) {
+    g_err[0] = 0;
+    if (check_plan(p) || !choices) return fail(GRIDSPT_E_INVALID, "plan/choices is NULL");
+    for (int i = 0; i < TV_COUNT; ++i)
+        if (choices[i] != 0 && choices[i] != 1) return fail(GRIDSPT_E_INVALID, "choice %d must be 0 or 1", i);
+    for (int i = 0; i < TV_COUNT; ++i) p->geo.var[i] = choices[i];
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_get_tuning(gridspt_plan p, int32_t* choices) {
+    if (check_plan(p) || !choices) return fail(GRIDSPT_E_INVALID, "plan/choices is NULL");
+    for (int i = 0; i < TV_COUNT; ++i) choices[i] = p->geo.var[i];
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_bytes, int32_t* choices_out,
+                                gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    size_t need = 0;
+    gridspt_autotune_scratch_size(p, &need);
+    if (!scratch || scratch_bytes < need || !aligned16(scratch))
+        return fail(GRIDSPT_E_INVALID, "scratch must be 16-byte aligned and >= %zu bytes", need);
+    if (gridspt_status st = set_device(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long F = field_c(p);
+    float2* f0 = static_cast<float2*>(scratch);
+    CK(cudaMemsetAsync(scratch, 0, need, s), "scratch clear");
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "event");
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_fail(e, "event");
+    }
+    // one representative launch per pass on fields 0..3
+    auto run = [&](const Geo& g, int pass) -> cudaError_t {
+        switch (pass) {
+            case TV_COLPASS: return launch_colpass_fwd(g, f0, F, 2, 1, 0, -1, s);
+            case TV_XEXP: {
+                XExpArgs xa{};
+                xa.src0 = f0;
+                xa.src1 = f0 + F;
+                xa.out = f0 + 2 * F;
+                xa.out_stride = F;
+                xa.nout = 2;
+                xa.codes[0] = x_code(XK_POW, 0, XS_DELTA);
+                xa.codes[1] = x_code(XK_POW, 1, XS_PHI);
+                xa.s2_nl = -1;
+                return launch_xexp(g, xa, s);
+            }
+            case TV_YEXP:
+            case TV_ZEXP: {
+                YZExpArgs ya{};
+                ya.in = f0 + 2 * F;
+                ya.in_stride = F;
+                ya.out = f0;
+                ya.out_stride = F;
+                ya.nout = 2;
+                ya.codes[0] = pass == TV_YEXP ? y_code(0, 0, 0) : z_code(0, 0, 0, 0);
+                ya.codes[1] = pass == TV_YEXP ? y_code(1, 1, 1) : z_code(1, 1, 1, 1);
+                return pass == TV_YEXP ? launch_yexp(g, ya, s) : launch_zexp(g, ya, s);
+            }
+            default: return launch_zr2c(g, f0 + 2 * F, f0 + 2 * F, F, 2, 1.0f, s);
+        }
+    };
+    int best[TV_COUNT];
+    for (int pass = 0; pass < TV_COUNT && e == cudaSuccess; ++pass) {
+        float tbest = 0.f;
+        best[pass] = 0;
+        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+            Geo g = p->geo;
+            g.var[pass] = v;
+            e = run(g, pass);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run(g, pass);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+            if (e == cudaSuccess && (v == 0 || t < tbest)) {
+                tbest = t;
+                best[pass] = v;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    for (int i = 0; i < TV_COUNT; ++i) {
+        p->geo.var[i] = best[i];
+        if (choices_out) choices_out[i] = best[i];
+    }
+    return GRIDSPT_OK;
+}
+
+// ---------------------------------------------------------- emulator MLP
+}  // extern "C"
+namespace {
+gridspt_status mlp_dims(int32_t in, int32_t hidden, int32_t out) {
+    if (in < 1 || in > 8 || hidden < 1 || hidden > 256 || out < 1 || out > 256)
+        return fail(GRIDSPT_E_INVALID, "mlp dims in=%d hidden=%d out=%d outside [1,8] x [1,256] x [1,256]", in,
+                    hidden, out);
+    return GRIDSPT_OK;
+}
+}  // namespace
+extern "C" {
+
+gridspt_status gridspt_mlp_param_count(int32_t in, int32_t hidden, int32_t out, int64_t* count) {
+    if (gridspt_status st = mlp_dims(in, hidden, out)) return st;
+    if (!count) return fail(GRIDSPT_E_INVALID, "count is NULL");
+    *count = mlp_params(in, hidden, out);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_mlp_forward(const float* x, int32_t batch, int32_t in, int32_t hidden, int32_t out,
+                                   const void* params, int32_t bf16, float* y, float* act, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (gridspt_status st = mlp_dims(in, hidden, out)) return st;
+    if (!x || !params || !y || batch < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or batch < 1");
+    CKP(PK_MLP_FWD, 4.0 * batch * (in + out) + (bf16 ? 2.0 : 4.0) * mlp_params(in, hidden, out), (cudaStream_t)stream,
+        launch_mlp_forward(x, batch, in, hidden, out, params, bf16, y, act, (cudaStream_t)stream), "mlp forward");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_mlp_backward_workspace_size(int32_t batch, int32_t in, int32_t hidden, int32_t out,
+                                                   size_t* bytes) {
+    if (gridspt_status st = mlp_dims(in, hidden, out)) return st;
+    if (!bytes || batch < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or batch < 1");
+    *bytes = sizeof(float) * (size_t)mlp_bwd_blocks(batch) * (size_t)mlp_params(in, hidden, out);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_mlp_backward(const float* x, int32_t batch, int32_t in, int32_t hidden, int32_t out,
+                                    const void* params, int32_t bf16, const float* act, const float* dy, float* grad,
+                                    void* ws, size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    size_t need = 0;
+    if (gridspt_status st = gridspt_mlp_backward_workspace_size(batch, in, hidden, out, &need)) return st;
+    if (!x || !params || !act || !dy || !grad) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!ws || ws_bytes < need) return fail(GRIDSPT_E_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    CKP(PK_MLP_BWD, 4.0 * batch * (in + 4 * hidden + out) + 4.0 * mlp_params(in, hidden, out), (cudaStream_t)stream,
+        launch_mlp_backward(x, batch, in, hidden, out, params, bf16, act, dy, static_cast<float*>(ws), grad,
+                            (cudaStream_t)stream),
+        "mlp backward");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_mlp_mse(const float* y, const float* target, const float* mask, int64_t n, float* dy,
+                               float* loss, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (!y || !target || !mask || !dy || n < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or n < 1");
+    CKP(PK_MLP_OPT, 16.0 * n, (cudaStream_t)stream, launch_mlp_mse(y, target, mask, n, dy, loss, (cudaStream_t)stream),
+        "mlp mse");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_mlp_adam(float* master, void* params_lowp, int32_t bf16, const float* grad, float* m, float* v,
+                                int32_t* step, int64_t n, float lr, float beta1, float beta2, float eps,
+                                gridspt_stream stream) {
+    g_err[0] = 0;
+    if (!master || !grad || !m || !v || !step || n < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or n < 1");
+    CKP(PK_MLP_OPT, 20.0 * n, (cudaStream_t)stream,
+        launch_mlp_adam(master, params_lowp, bf16, grad, m, v, step, n, lr, beta1, beta2, eps, (cudaStream_t)stream),
+        "mlp adam");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_mlp_convert(const float* master, void* params_lowp, int32_t bf16, int64_t n,
+                                   gridspt_stream stream) {
+    g_err[0] = 0;
+    if (!master || !params_lowp || n < 1) return fail(GRIDSPT_E_INVALID, "NULL argument or n < 1");
+    CK(launch_mlp_convert(master, params_lowp, bf16, n, (cudaStream_t)stream), "mlp convert");
     return GRIDSPT_OK;
 }
 

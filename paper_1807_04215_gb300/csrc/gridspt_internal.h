@@ -126,6 +126,19 @@ cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks,
 
 bool supported_n(int N);
 
+// emulator network (k_mlp.cu)
+long long mlp_params(int I, int H, int O);
+int mlp_bwd_blocks(int B);
+cudaError_t launch_mlp_forward(const float* x, int B, int I, int H, int O, const void* theta, int bf16, float* y,
+                               float* act, cudaStream_t s);
+cudaError_t launch_mlp_backward(const float* x, int B, int I, int H, int O, const void* theta, int bf16,
+                                const float* act, const float* dy, float* part, float* grad, cudaStream_t s);
+cudaError_t launch_mlp_mse(const float* y, const float* t, const float* mask, long long n, float* dy, float* loss,
+                           cudaStream_t s);
+cudaError_t launch_mlp_adam(float* master, void* lowp, int bf16, const float* grad, float* m, float* v, int* step,
+                            long long n, float lr, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t launch_mlp_convert(const float* src, void* dst, int bf16, long long n, cudaStream_t s);
+
 // Library-owned scratch of the allocation-free power entry point
 // (k_power_static.cu): device address of the static array on the current
 // device (looked up once per device), its size, and whether a request fits.

@@ -109,6 +109,73 @@ def run_orders(plan, delta1, start_order=2, spectra=None, ws=None):
     return spectra
 
 
+class Batch:
+    """gridspt_batch: the recursion of several plans (sizes may differ) captured
+    as one CUDA graph; launch() replays it with one graph launch. Keeps the
+    tensors it was built on alive (their addresses are baked into the graph)."""
+
+    def __init__(self, plans, delta1s, spectra=None, wss=None, start_orders=None):
+        self.lib = _lib.load()
+        n = len(plans)
+        spectra = list(spectra) if spectra is not None else [
+            torch.empty(p.half_shape(p.batch, p.n_max - 1, 2), dtype=torch.complex64, device="cuda") for p in plans]
+        wss = list(wss) if wss is not None else [
+            torch.empty(max(p.workspace_size(), 16), dtype=torch.uint8, device="cuda") for p in plans]
+        starts = list(start_orders) if start_orders is not None else [2] * n
+        for p, d, sp in zip(plans, delta1s, spectra):
+            p._check_half(d, (p.batch,), "delta1")
+            p._check_half(sp, (p.batch, p.n_max - 1, 2), "spectra")
+        self.keep = (plans, list(delta1s), spectra, wss)
+        arr = lambda T, xs: (T * n)(*xs)  # noqa: E731
+        h = ctypes.c_void_p()
+        _lib.check("gridspt_batch_create", self.lib.gridspt_batch_create(
+            arr(ctypes.c_void_p, [p.handle.value for p in plans]), n,
+            arr(ctypes.c_void_p, [d.data_ptr() for d in delta1s]), arr(ctypes.c_int32, starts),
+            arr(ctypes.c_void_p, [x.data_ptr() for x in spectra]), arr(ctypes.c_void_p, [w.data_ptr() for w in wss]),
+            arr(ctypes.c_size_t, [w.numel() for w in wss]), ctypes.byref(h)))
+        self.handle = h
+        self.spectra = spectra
+
+    def launch(self):
+        _lib.check("gridspt_batch_launch", self.lib.gridspt_batch_launch(self.handle, _stream()))
+        return self.spectra
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.check("gridspt_batch_destroy", self.lib.gridspt_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(plan, scratch=None):
+    """Time both tile variants of every transform pass and keep the faster;
+    returns the choices [column pass, x, y, z expansion, z forward]."""
+    b = ctypes.c_size_t()
+    _lib.check("gridspt_autotune_scratch_size", plan.lib.gridspt_autotune_scratch_size(plan.handle, ctypes.byref(b)))
+    if scratch is None:
+        scratch = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    ch = (ctypes.c_int32 * 5)()
+    _lib.check("gridspt_autotune", plan.lib.gridspt_autotune(plan.handle, _ptr(scratch), scratch.numel(), ch,
+                                                              _stream()))
+    return list(ch)
+
+
+def set_tuning(plan, choices):
+    ch = (ctypes.c_int32 * 5)(*[int(c) for c in choices])
+    _lib.check("gridspt_set_tuning", plan.lib.gridspt_set_tuning(plan.handle, ch))
+
+
+def get_tuning(plan):
+    ch = (ctypes.c_int32 * 5)()
+    _lib.check("gridspt_get_tuning", plan.lib.gridspt_get_tuning(plan.handle, ch))
+    return list(ch)
+
+
 def c2r(plan, spec, out=None):
     lead = tuple(spec.shape[:-3])
     count = int(math.prod(lead)) if lead else 1
@@ -217,3 +284,64 @@ def profile_end():
     n = ctypes.c_int32()
     _lib.check("gridspt_profile_end", lib.gridspt_profile_end(arr, cap, ctypes.byref(n)))
     return {arr[i].name.decode(): (arr[i].launches, arr[i].ms, arr[i].bytes) for i in range(n.value)}
+
+
+# ---------------------------------------------------------------- emulator MLP
+class MLP:
+    """Device buffers and kernel calls of the emulator network (C-ABI
+    gridspt_mlp_*): FP32 master parameters, the bf16 (or FP32) copy read by
+    forward/backward, Adam moments and the device step counter."""
+
+    def __init__(self, n_in=3, hidden=128, n_out=160, bf16=True, seed=0):
+        self.lib = _lib.load()
+        self.I, self.H, self.O, self.bf16 = n_in, hidden, n_out, int(bool(bf16))
+        c = ctypes.c_int64()
+        _lib.check("gridspt_mlp_param_count", self.lib.gridspt_mlp_param_count(n_in, hidden, n_out, ctypes.byref(c)))
+        self.n = c.value
+        # Glorot-uniform weights, zero biases (initial values from a seeded torch generator)
+        gen = torch.Generator().manual_seed(seed)
+        parts = []
+        for fi, fo in ((n_in, hidden), (hidden, hidden), (hidden, n_out)):
+            lim = math.sqrt(6.0 / (fi + fo))
+            parts += [(torch.rand(fi * fo, generator=gen) * 2 - 1) * lim, torch.zeros(fo)]
+        self.master = torch.cat(parts).to(torch.float32).cuda()
+        self.lowp = torch.empty(self.n, dtype=torch.bfloat16 if self.bf16 else torch.float32, device="cuda")
+        self.m = torch.zeros(self.n, dtype=torch.float32, device="cuda")
+        self.v = torch.zeros(self.n, dtype=torch.float32, device="cuda")
+        self.step = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.grad = torch.zeros(self.n, dtype=torch.float32, device="cuda")
+        self.sync_lowp()
+
+    def sync_lowp(self):
+        _lib.check("gridspt_mlp_convert", self.lib.gridspt_mlp_convert(_ptr(self.master), _ptr(self.lowp), self.bf16,
+                                                                        self.n, _stream()))
+
+    def forward(self, x, y=None, act=None):
+        B = x.shape[0]
+        if y is None:
+            y = torch.empty(B, self.O, dtype=torch.float32, device="cuda")
+        _lib.check("gridspt_mlp_forward", self.lib.gridspt_mlp_forward(
+            _ptr(x), B, self.I, self.H, self.O, _ptr(self.lowp), self.bf16, _ptr(y), _ptr(act), _stream()))
+        return y
+
+    def ws_bytes(self, B):
+        b = ctypes.c_size_t()
+        _lib.check("gridspt_mlp_backward_workspace_size",
+                   self.lib.gridspt_mlp_backward_workspace_size(B, self.I, self.H, self.O, ctypes.byref(b)))
+        return b.value
+
+    def backward(self, x, act, dy, ws):
+        _lib.check("gridspt_mlp_backward", self.lib.gridspt_mlp_backward(
+            _ptr(x), x.shape[0], self.I, self.H, self.O, _ptr(self.lowp), self.bf16, _ptr(act), _ptr(dy),
+            _ptr(self.grad), _ptr(ws), ws.numel(), _stream()))
+        return self.grad
+
+    def mse(self, y, t, mask, dy, loss=None):
+        _lib.check("gridspt_mlp_mse", self.lib.gridspt_mlp_mse(_ptr(y), _ptr(t), _ptr(mask), y.numel(), _ptr(dy),
+                                                                _ptr(loss), _stream()))
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        _lib.check("gridspt_mlp_adam", self.lib.gridspt_mlp_adam(
+            _ptr(self.master), _ptr(self.lowp), self.bf16, _ptr(self.grad), _ptr(self.m), _ptr(self.v),
+            _ptr(self.step), self.n, ctypes.c_float(lr), ctypes.c_float(b1), ctypes.c_float(b2), ctypes.c_float(eps),
+            _stream()))

@@ -1,0 +1,59 @@
+"""Launch batching and autotuning (not part of the paper's method): a CUDA
+graph of the whole recursion and a mixed-size batch in one graph launch must
+reproduce the eager launches bit for bit; tile variants chosen by the
+autotuner must not change any result."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1807_04215_gb300 import gridspt as g  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_single_plan_graph_equals_eager():
+    plan = g.Plan(64, 5, 500.0, batch=2)
+    d1 = g.make_linear_field(plan, [11, 12])
+    eager = g.run_orders(plan, d1)
+    b = g.Batch([plan], [d1])
+    out = b.launch()[0]
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+    out.zero_()
+    b.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)          # replay recomputes everything
+    b.close()
+
+
+def test_mixed_size_batch_one_launch_equals_separate_runs():
+    sizes = [(32, 250.0), (48, 375.0), (64, 500.0)]   # same cell size, as in the mixed workload
+    plans = [g.Plan(n, 5, L, batch=2) for n, L in sizes]
+    d1s = [g.make_linear_field(p, [100 + i, 200 + i]) for i, p in enumerate(plans)]
+    ref = [g.run_orders(p, d) for p, d in zip(plans, d1s)]
+    b = g.Batch(plans, d1s)
+    outs = b.launch()
+    torch.cuda.synchronize()
+    for r, o in zip(ref, outs):
+        assert torch.equal(r, o)
+    b.close()
+
+
+@pytest.mark.parametrize("N", [128, 192])
+def test_tile_variants_give_identical_results(N):
+    plan = g.Plan(N, 3, 4.0 * N)
+    d1 = g.make_linear_field(plan, [5])
+    results = []
+    for choice in ([0] * 5, [1] * 5):
+        g.set_tuning(plan, choice)
+        assert g.get_tuning(plan) == choice
+        results.append(g.run_orders(plan, d1).clone())
+        torch.cuda.synchronize()
+    assert torch.equal(results[0], results[1])
+    ch = g.autotune(plan)
+    assert len(ch) == 5 and all(c in (0, 1) for c in ch)
+    assert g.get_tuning(plan) == ch
+    assert torch.equal(g.run_orders(plan, d1), results[0])

@@ -362,3 +362,55 @@ def test_bispectrum_fft_estimator_equals_triangle_enumeration():
         cnt = sum(1 for p in vecs for q in vecs
                   if (-(p[0] + q[0]), -(p[1] + q[1]), -(p[2] + q[2])) in vs)
         assert round(nt[i]) == cnt
+
+
+# ------------------------------------------------------------ emulator MLP
+def test_mlp_backward_matches_finite_differences():
+    """The oracle's analytic gradient against central differences of its own
+    forward pass (catches a transposed weight or a wrong SiLU derivative)."""
+    from oracle import mlp
+    H, O, B = 7, 5, 6
+    g = inputs.rng(3)
+    theta = g.standard_normal(mlp.n_params(H, O)) * 0.5
+    x = g.standard_normal((B, 3))
+    t = g.standard_normal((B, O))
+    mask = (g.random((B, O)) > 0.2).astype(float)
+    y, acts = mlp.forward(x, theta, H, O)
+    L, dy = mlp.masked_mse(y, t, mask)
+    grad = mlp.backward(x, theta, H, O, acts, dy)
+    h = 1e-6
+    for i in g.choice(theta.size, 40, replace=False):
+        e = np.zeros_like(theta)
+        e[i] = h
+        Lp = mlp.masked_mse(mlp.forward(x, theta + e, H, O)[0], t, mask)[0]
+        Lm = mlp.masked_mse(mlp.forward(x, theta - e, H, O)[0], t, mask)[0]
+        assert abs((Lp - Lm) / (2 * h) - grad[i]) < 1e-7 * max(1.0, abs(grad[i]))
+
+
+def test_silu_and_derivative_closed_values():
+    from oracle import mlp
+    assert mlp.silu(np.array([0.0]))[0] == 0.0
+    assert abs(mlp.silu(np.array([1.0]))[0] - 1.0 / (1.0 + math.exp(-1.0))) < 1e-15
+    assert abs(mlp.silu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+    # large |z|: SiLU -> z (slope 1) and -> 0 (slope 0)
+    assert abs(mlp.silu_grad(np.array([40.0]))[0] - 1.0) < 1e-12
+    assert abs(mlp.silu_grad(np.array([-40.0]))[0]) < 1e-12
+
+
+def test_adam_first_step_is_sign_step():
+    """With m = v = 0, the bias-corrected first Adam step is lr * g / (|g| + eps)."""
+    from oracle import mlp
+    th = np.array([1.0, -2.0, 0.5])
+    gr = np.array([0.3, -4.0, 1e-3])
+    new, m, v = mlp.adam_step(th, gr, np.zeros(3), np.zeros(3), 1, 0.01)
+    assert np.allclose(new, th - 0.01 * gr / (np.abs(gr) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_bf16_rounding_ties_and_range():
+    from oracle import mlp
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even -> 1
+    assert mlp.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert mlp.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    assert mlp.bf16_round(np.array([1.0 + 2.0 ** -7]))[0] == 1.0 + 2.0 ** -7
+    x = inputs.rng(1).standard_normal(1000)
+    assert np.max(np.abs(mlp.bf16_round(x) / x - 1)) <= 2.0 ** -8
