@@ -174,7 +174,11 @@ gridspt_status gridspt_power_noalloc(gridspt_plan plan, const void* a_k, const v
  * tree-level bispectrum is B_tree = 3 e_out for a = delta_1, b = delta_2.
  *   edges: HOST double[nbins+1] with edges[nbins] <= 2 k_Ny / 3 (no wrap);
  *   e_out, ntri_out: device double[nbins]; 1 <= nbins <= 64. FP32 fields,
- *   FP64 sums. ws: gridspt_bispectrum_workspace_size bytes of device scratch. */
+ *   Kahan FP32 / FP64 sums. ws: gridspt_bispectrum_workspace_size bytes of
+ *   device scratch. sum_x J^3 does not depend on the data: the first call
+ *   with a given set of shells computes it and keeps it in the plan (device
+ *   memory), later calls with the same shells reuse it, so they must be
+ *   ordered after that first call (same stream, or synchronised). */
 gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan plan, int32_t nbins, size_t* bytes);
 gridspt_status gridspt_bispectrum(gridspt_plan plan, const void* a_k, const void* b_k,
                                   int32_t nbins, const double* edges, double* e_out,

@@ -28,6 +28,9 @@ struct gridspt_plan_s {
     int device = 0;
     long long pb_top = -1;  // cache of the last power-launch byte count (profiling only)
     double pb_modes = 0.0;
+    double* j3 = nullptr;   // device [kMaxBins]: sum_x J^3 per bispectrum shell (data independent)
+    int j3_nb = 0;          // shells the cache holds (0: empty) and their thresholds
+    int j3_thr[kMaxBins + 1] = {};
 };
 
 namespace {
@@ -258,8 +261,14 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     }
     e = cudaMalloc(&p->tw, sizeof(float2) * N);
     if (e != cudaSuccess) { delete p; return fail(GRIDSPT_E_NOMEM, "twiddle table: %s", cudaGetErrorString(e)); }
+    e = cudaMalloc(&p->j3, sizeof(double) * kMaxBins);
+    if (e != cudaSuccess) {
+        cudaFree(p->tw);
+        delete p;
+        return fail(GRIDSPT_E_NOMEM, "shell cache: %s", cudaGetErrorString(e));
+    }
     e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaFree(p->tw); delete p; return cuda_fail(e, "twiddle upload"); }
+    if (e != cudaSuccess) { cudaFree(p->tw); cudaFree(p->j3); delete p; return cuda_fail(e, "twiddle upload"); }
     p->geo.tw = p->tw;
     *out = p;
     return GRIDSPT_OK;
@@ -271,6 +280,8 @@ gridspt_status gridspt_plan_destroy(gridspt_plan p) {
     if (p->tw) {
         e = cudaDeviceSynchronize();
         cudaError_t e2 = cudaFree(p->tw);
+        if (e == cudaSuccess) e = e2;
+        e2 = p->j3 ? cudaFree(p->j3) : cudaSuccess;
         if (e == cudaSuccess) e = e2;
     }
     delete p;
@@ -949,22 +960,32 @@ gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b
     const double L = p->d.box;
     const long long fstride = (long long)(fb / sizeof(float2));
     const int G = shell_blocks(p->geo);
+    // sum J^3 per shell is data independent: reuse it when the shells match the cached ones
+    bool cached = p->j3_nb == nbins;
+    for (int i = 0; cached && i <= nbins; ++i) cached = p->j3_thr[i] == bs.thr[i];
+    const int nf = cached ? 2 : 3;
     for (int i = 0; i < nbins; ++i) {
         if (bs.thr[i + 1] <= 1) {   // shell holds no mode with k > 0
             CK(cudaMemsetAsync(e_out + i, 0, sizeof(double), s), "bispectrum empty shell");
             CK(cudaMemsetAsync(ntri_out + i, 0, sizeof(double), s), "bispectrum empty shell");
+            if (!cached) CK(cudaMemsetAsync(p->j3 + i, 0, sizeof(double), s), "bispectrum empty shell");
             continue;
         }
         // every mode of the shell has |s_a| < band in each component
         const int band = (int)std::floor(std::sqrt((double)(bs.thr[i + 1] - 1))) + 1;
         if (gridspt_status st = backward_fields(p, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k),
-                                                fields, fstride, 3, true, bs.thr[i], bs.thr[i + 1], band, true, s))
+                                                fields, fstride, nf, true, bs.thr[i], bs.thr[i + 1], band, true, s))
             return st;
         const double fbytes = 4.0 * (double)field_floats(p);
-        CKP(PK_BZ, fbytes * 3 * ((double)band / p->geo.M), s, launch_zshell(p->geo, fields, fstride, band, partial, s),
-            "bispectrum z pass and sums");
-        CK(launch_bispec_final(p->geo, partial, G, e_out + i, ntri_out + i, L * L * L * L * L * L, s),
-           "bispectrum final sum");
+        CKP(PK_BZ, fbytes * nf * ((double)band / p->geo.M), s,
+            launch_zshell(p->geo, fields, fstride, band, nf, partial, s), "bispectrum z pass and sums");
+        CKP(PK_BISPEC, 16.0 * G, s,
+            launch_bispec_final(p->geo, partial, G, nf, p->j3 + i, e_out + i, ntri_out + i, L * L * L * L * L * L, s),
+            "bispectrum final sum");
+    }
+    if (!cached) {
+        p->j3_nb = nbins;
+        for (int i = 0; i <= nbins; ++i) p->j3_thr[i] = bs.thr[i];
     }
     return GRIDSPT_OK;
 }

@@ -115,14 +115,16 @@ int power_blocks(const Geo& g);
 cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const BinSpec& bins,
                          double* partial, double* p_out, int64_t* nk_out, double volume,
                          cudaStream_t s);
-// Bispectrum, one shell: z transform of the three xy-fields (I_a, I_b, J with
-// kz < band) fused with the sums of I_a^2 I_b and J^3 (per-block partials),
-// then the fixed-order final reduction.
+// Bispectrum, one shell: z transform of the xy-fields I_a, I_b (and J when
+// nfields = 3; kz < band) fused with the sums of I_a^2 I_b (and J^3), per-block
+// partials, then the fixed-order final reduction. sum J^3 does not depend on
+// the data: with nfields = 3 the final kernel stores it in *j3_cache, with 2
+// it reads it from there.
 int shell_blocks(const Geo& g);
-cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, double* partial,
-                          cudaStream_t s);
-cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, double* e_out,
-                                double* ntri_out, double vol2, cudaStream_t s);
+cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, int nfields,
+                          double* partial, cudaStream_t s);
+cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, int nfields, double* j3_cache,
+                                double* e_out, double* ntri_out, double vol2, cudaStream_t s);
 
 bool supported_n(int N);
 

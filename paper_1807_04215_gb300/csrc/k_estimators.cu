@@ -147,8 +147,8 @@ cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const B
 // Final reduction of the per-block partials written by k_zshell (one shell):
 // E = L^6 sum I_a^2 I_b / sum J^3, N_tri = sum J^3 / N^3; one block, fixed order.
 __global__ void __launch_bounds__(256)
-k_bispec_final(const double* __restrict__ partial, int G, double vol2, double cells,
-               double* __restrict__ e_out, double* __restrict__ ntri_out) {
+k_bispec_final(const double* __restrict__ partial, int G, int nfields, double* __restrict__ j3_cache, double vol2,
+               double cells, double* __restrict__ e_out, double* __restrict__ ntri_out) {
     __shared__ double r1[256], r2[256];
     double s1 = 0.0, s2 = 0.0;
     for (int g = threadIdx.x; g < G; g += 256) {
@@ -166,15 +166,19 @@ k_bispec_final(const double* __restrict__ partial, int G, double vol2, double ce
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double nt = r2[0] / cells;
+        double j3 = r2[0];
+        if (nfields == 3) *j3_cache = j3;
+        else j3 = *j3_cache;
+        const double nt = j3 / cells;
         *ntri_out = nt;
-        *e_out = nt > 0.5 ? vol2 * r1[0] / r2[0] : 0.0;
+        *e_out = nt > 0.5 ? vol2 * r1[0] / j3 : 0.0;
     }
 }
 
-cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, double* e_out,
-                                double* ntri_out, double vol2, cudaStream_t s) {
-    k_bispec_final<<<1, 256, 0, s>>>(partial, blocks, vol2, (double)g.N * g.N * g.N, e_out, ntri_out);
+cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, int nfields, double* j3_cache,
+                                double* e_out, double* ntri_out, double vol2, cudaStream_t s) {
+    k_bispec_final<<<1, 256, 0, s>>>(partial, blocks, nfields, j3_cache, vol2, (double)g.N * g.N * g.N, e_out,
+                                     ntri_out);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,33 @@ __device__ __forceinline__ void load_table(float2* tw, const float2* __restrict_
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
 }
 
+// Asynchronous 8-byte global -> shared copies (cp.async, Ampere and later);
+// src_bytes = 0 fills the destination with zeros.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Issue (without waiting) the copy of TZ rows of M float2 into a shared tile.
+template <int M, int TZ, int PITCH, int NTHR>
+__device__ __forceinline__ void tile_prefetch(float2* tile, const float2* src, long long row0, long long rows) {
+    constexpr int NV = TZ * M;
+    constexpr int PER = (NV + NTHR - 1) / NTHR;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NTHR;
+        if (idx < NV) {
+            const int r = idx / M, j = idx - r * M;
+            const long long row = row0 + r;
+            const bool ok = row < rows;
+            cp_async8(tile + r * PITCH + j, src + (ok ? row * M + j : 0), ok ? 8 : 0);
+        }
+    }
+    cp_async_commit();
+}
+
 // Copy TZ contiguous rows of M float2 between global memory and a shared tile
 // of odd pitch PITCH. Consecutive threads move consecutive float2 of a row
 // (coalesced, conflict-free); all loads are issued before the shared stores,
@@ -325,26 +352,34 @@ k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
 template <int N, int TZ>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
 k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
-    constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH;
+    constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NT = TZ * P;
     extern __shared__ float2 sm[];
     float2* tw = sm;
-    float2* tin = sm + N;
-    float2* tex = tin + TZ * PITCH;
+    float2* tin[2] = {sm + N, sm + N + TZ * PITCH};   // double-buffered input tiles
+    float2* tex = sm + N + 2 * TZ * PITCH;            // output tile / exchange buffer
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
-    int cur = -1;
+    // prefetch the first input
+    tile_prefetch<M, TZ, PITCH, NT>(tin[0], args.in + (args.codes[0] & 255) * args.in_stride, row0, rows);
+    int cur = args.codes[0] & 255, buf = 0;
     for (int f = 0; f < args.nout; ++f) {
         const int code = args.codes[f];
         const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
-        __syncthreads();                       // tin / tex free for reuse
-        if (in != cur) {
-            tile_load<M, TZ, PITCH, TZ * P>(tin, args.in + in * args.in_stride, row0, rows);
-            __syncthreads();
+        if (f == 0 || in != cur) {
+            if (f > 0) buf ^= 1;
             cur = in;
+            cp_async_wait_all();
+            __syncthreads();   // tile complete and visible; the other buffer is no longer read
+            // prefetch the next distinct input while this one's outputs are formed
+            int nf = f + 1;
+            while (nf < args.nout && (args.codes[nf] & 255) == in) ++nf;
+            if (nf < args.nout)
+                tile_prefetch<M, TZ, PITCH, NT>(tin[buf ^ 1], args.in + (args.codes[nf] & 255) * args.in_stride,
+                                                row0, rows);
         }
-        const float2* colp = tin + c * PITCH;
+        const float2* colp = tin[buf] + c * PITCH;
         float2 x[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -368,13 +403,15 @@ k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
             const float2 Ov = cmul(csub(Xk, Xm), tw[k]);     // e^{+2 pi i k / N}
             x[i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);    // E + i O
         }
+        __syncthreads();                                     // tex free (previous store done reading)
         float2* colx = tex + c * PITCH;
         fft_column<M, +1, N>(x, p, colx, 1, tw);
 #pragma unroll
         for (int i = 0; i < E; ++i) colx[p + P * i] = x[i];
         __syncthreads();
-        tile_store<M, TZ, PITCH, TZ * P>(args.out + slot * args.out_stride, tex, row0, rows);
+        tile_store<M, TZ, PITCH, NT>(args.out + slot * args.out_stride, tex, row0, rows);
     }
+    cp_async_wait_all();
 }
 
 // ------------------------------------------- z pass fused with the shell sums
@@ -390,7 +427,7 @@ __device__ __forceinline__ void kahan_add2(float& s, float& c, float x) {
     s = t;
 }
 
-template <int N, int TZ>
+template <int N, int TZ, int NF>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
 k_zshell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
          double* __restrict__ partial) {
@@ -404,20 +441,25 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
     const int B = band < M ? band : M;
-    // load kz < B of the three fields; zero the rest of each tile row
-    for (int f = 0; f < 3; ++f) {
+    // kz < B of each field (asynchronous copies), zeros elsewhere
+    for (int f = 0; f < NF; ++f) {
         const float2* src = in + f * in_stride;
         float2* tile = t3 + f * TZ * PITCH;
         for (int idx = tid; idx < TZ * M; idx += NT) {
             const int r = idx / M, j = idx - r * M;
             const long long row = row0 + r;
-            tile[r * PITCH + j] = (j < B && row < rows) ? src[row * M + j] : make_float2(0.f, 0.f);
+            if (j < B && row < rows)
+                cp_async8(tile + r * PITCH + j, src + row * M + j, 8);
+            else
+                tile[r * PITCH + j] = make_float2(0.f, 0.f);
         }
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
-    float2 x[3][E];
+    float2 x[NF][E];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
+    for (int f = 0; f < NF; ++f) {
         const float2* colp = t3 + f * TZ * PITCH + c * PITCH;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -431,14 +473,17 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     }
     __syncthreads();
 #pragma unroll
-    for (int f = 0; f < 3; ++f) fft_column<M, +1, N>(x[f], p, t3 + f * TZ * PITCH + c * PITCH, 1, tw);
+    for (int f = 0; f < NF; ++f) fft_column<M, +1, N>(x[f], p, t3 + f * TZ * PITCH + c * PITCH, 1, tw);
     float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
     if (row0 + c < rows) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            const float2 a = x[0][i], b = x[1][i], j = x[2][i];   // cells 2n, 2n + 1
+            const float2 a = x[0][i], b = x[1][i];   // cells 2n, 2n + 1
             kahan_add2(s1, c1, a.x * a.x * b.x + a.y * a.y * b.y);
-            kahan_add2(s2, c2, j.x * j.x * j.x + j.y * j.y * j.y);
+            if constexpr (NF == 3) {
+                const float2 j = x[NF - 1][i];
+                kahan_add2(s2, c2, j.x * j.x * j.x + j.y * j.y * j.y);
+            }
         }
     }
     double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
@@ -533,19 +578,24 @@ struct Launch {
     static cudaError_t zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
         const long long rows = (long long)N * N;
         dim3 grid((unsigned)((rows + TZZ - 1) / TZZ));
-        const size_t smem = sizeof(float2) * (N + 2 * (size_t)TZZ * PITCH);
+        const size_t smem = sizeof(float2) * (N + 3 * (size_t)TZZ * PITCH);
         cudaError_t e = set_smem(k_zexp<N, TZZ>, smem);
         if (e != cudaSuccess) return e;
         k_zexp<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
         return cudaGetLastError();
     }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
-    static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, double* partial,
+    static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, double* partial,
                               cudaStream_t s) {
-        const size_t smem = sizeof(float2) * (N + 3 * (size_t)TZZ * PITCH);
-        cudaError_t e = set_smem(k_zshell<N, TZZ>, smem);
-        if (e != cudaSuccess) return e;
-        k_zshell<N, TZZ><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
+        const size_t smem = sizeof(float2) * (N + (size_t)nf * TZZ * PITCH);
+        cudaError_t e;
+        if (nf == 3) {
+            if ((e = set_smem(k_zshell<N, TZZ, 3>, smem)) != cudaSuccess) return e;
+            k_zshell<N, TZZ, 3><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
+        } else {
+            if ((e = set_smem(k_zshell<N, TZZ, 2>, smem)) != cudaSuccess) return e;
+            k_zshell<N, TZZ, 2><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
+        }
         return cudaGetLastError();
     }
 };
@@ -576,9 +626,9 @@ struct Launch {
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zexp(g, a, s);                                   \
     }                                                                                                      \
     int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
-    cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band,               \
+    cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band, int nf,       \
                                      double* partial, cudaStream_t s) {                                    \
-        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zshell(g, in, st, band, partial, s);                 \
+        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zshell(g, in, st, band, nf, partial, s);             \
     }
 
 }  // namespace gridspt

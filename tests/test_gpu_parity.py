@@ -299,3 +299,21 @@ def test_bispectrum_matches_oracle(N, L, nb):
     E = E.cpu().numpy()
     sel = ntr > 0.5
     assert np.all(np.abs(E[sel] - Er[sel]) <= 1e-4 * np.abs(Er[sel]).max())
+
+
+def test_bispectrum_reuses_shell_normalisation_across_calls():
+    """The first call stores sum J^3 per shell in the plan; repeated calls with
+    the same shells reuse it and agree bit for bit; new shells recompute."""
+    N, L, nb = 48, 300.0, 6
+    plan = g.Plan(N, 3, L)
+    d1 = g.make_linear_field(plan, [4])
+    sp = g.run_orders(plan, d1)
+    kc = 2 * math.pi / L * N / 4
+    e1 = [kc * i / nb for i in range(nb + 1)]
+    e2 = [kc * (0.5 + i) / (nb + 1) for i in range(nb + 1)]
+    first = [t.clone() for t in g.bispectrum(plan, d1[0], sp[0, 0, 0], e1)]
+    again = g.bispectrum(plan, d1[0], sp[0, 0, 0], e1)
+    assert torch.equal(first[0], again[0]) and torch.equal(first[1], again[1])
+    other = g.bispectrum(plan, d1[0], sp[0, 0, 0], e2)
+    fresh = g.bispectrum(g.Plan(N, 3, L), d1[0], sp[0, 0, 0], e2)
+    assert torch.equal(other[0], fresh[0]) and torch.equal(other[1], fresh[1])
