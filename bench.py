@@ -52,6 +52,27 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# --------------------------------------------------------- replica helpers
+def rank_seeds(rank, per_rank):
+    """Realisations are independent: rank r runs seeds 1000 + r * B .. + B - 1."""
+    return [1000 + rank * per_rank + i for i in range(per_rank)]
+
+
+def max_over_ranks(value, dist, device):
+    """Slowest rank's time (the job is done when every replica is done)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(world, per_rank, n, n_max, ms):
+    """Whole-job Mcells*orders/s: all ranks' realisations over the slowest rank's time."""
+    return world * per_rank * n ** 3 * n_max / 1e6 / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     def __init__(self, index):
@@ -150,7 +171,7 @@ def run_gpu(args, rank, world):
     N, B = args.n, args.batch
     L = BOX * N / N_GRID
     plan = g.Plan(N, N_MAX, L, batch=B)
-    seeds = [1000 + rank * B + r for r in range(B)]
+    seeds = rank_seeds(rank, B)
     d1 = torch.empty(plan.half_shape(B), dtype=torch.complex64, device="cuda")
     spectra = torch.empty(plan.half_shape(B, N_MAX - 1, 2), dtype=torch.complex64, device="cuda")
     ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device="cuda")
@@ -198,11 +219,8 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     prof = g.profile_end()
     clk = clocks.stop() if clocks else None
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
 
     # end to end through the public API: delta_1(k) from pinned host memory in,
@@ -225,11 +243,7 @@ def run_gpu(args, rank, world):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, dist, "cuda")
 
     mixed = mixed_batch(args) if rank == 0 and not args.quick else None
     emu = emulator_section(args) if rank == 0 and not args.quick else None
@@ -238,7 +252,7 @@ def run_gpu(args, rank, world):
             dist.destroy_process_group()
         return
     work = world * B * N ** 3 * N_MAX / 1e6
-    value = work / (ms / 1e3)
+    value = aggregate_throughput(world, B, N, N_MAX, ms)
     # dominant kernel by summed device time
     kname, (nl, kms, kbytes) = max(prof.items(), key=lambda kv: kv[1][1])
     peak, src = peaks()

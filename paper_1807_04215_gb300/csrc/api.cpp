@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <mutex>
@@ -57,6 +58,22 @@ gridspt_status cuda_fail(cudaError_t e, const char* where) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Host-side fault injection for tests (no GPU fault is ever caused): the
+// environment variable GRIDSPT_FAULT_INJECT holds a comma-separated list of
+//   plan_alloc  - the plan's second device allocation reports out-of-memory
+//   launch      - every kernel launch reports a launch failure without launching
+bool fault_inject(const char* what) {
+    const char* v = std::getenv("GRIDSPT_FAULT_INJECT");
+    if (!v || !*v) return false;
+    const size_t n = std::strlen(what);
+    for (const char* q = v; (q = std::strstr(q, what)) != nullptr; q += n) {
+        const bool start = q == v || q[-1] == ',';
+        const bool end = q[n] == 0 || q[n] == ',';
+        if (start && end) return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------- profiling
 enum ProfKind {
     PK_IC, PK_XEXP, PK_XEXP_FWD, PK_YEXP, PK_ZEXP, PK_Y_FWD, PK_X_FWD, PK_ZR2C,
@@ -96,6 +113,7 @@ cudaEvent_t prof_event() {
 // Launch through `f`, bracketed by events on `s` while profiling is on.
 template <class F>
 cudaError_t prof_launch(int kind, double bytes, cudaStream_t s, F&& f) {
+    if (fault_inject("launch")) return cudaErrorLaunchFailure;
     std::unique_lock<std::mutex> lk(g_prof.mu);
     if (!g_prof.on || t_capturing || g_prof.recs.size() >= kMaxProfRecs) {
         lk.unlock();
@@ -261,7 +279,7 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     }
     e = cudaMalloc(&p->tw, sizeof(float2) * N);
     if (e != cudaSuccess) { delete p; return fail(GRIDSPT_E_NOMEM, "twiddle table: %s", cudaGetErrorString(e)); }
-    e = cudaMalloc(&p->j3, sizeof(double) * kMaxBins);
+    e = fault_inject("plan_alloc") ? cudaErrorMemoryAllocation : cudaMalloc(&p->j3, sizeof(double) * kMaxBins);
     if (e != cudaSuccess) {
         cudaFree(p->tw);
         delete p;

@@ -27,7 +27,9 @@ __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 // Tile widths. Variant 0 is the default; variant 1 is the alternative the
-// autotuner also times (only instantiated separately for N >= 128).
+// autotuner also times (only instantiated separately for N >= 128). For the z
+// expansion the alternative keeps the tile width and instead prefetches the
+// next input tile with cp.async.
 template <int N>
 struct Cfg {
     static constexpr int M = N / 2;
@@ -349,35 +351,42 @@ k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
 // input tile of 16+ rows is loaded once per input (tin) and kept while its
 // outputs are formed in a second tile (tex), which is also the transform's
 // exchange buffer.
-template <int N, int TZ>
+template <int N, int TZ, bool PREFETCH>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
 k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
     constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NT = TZ * P;
     extern __shared__ float2 sm[];
     float2* tw = sm;
-    float2* tin[2] = {sm + N, sm + N + TZ * PITCH};   // double-buffered input tiles
-    float2* tex = sm + N + 2 * TZ * PITCH;            // output tile / exchange buffer
+    // input tiles (two when the next input is prefetched with cp.async) and the
+    // output tile, which is also the transform's exchange buffer
+    float2* tin[2] = {sm + N, sm + N + (PREFETCH ? TZ * PITCH : 0)};
+    float2* tex = sm + N + (PREFETCH ? 2 : 1) * TZ * PITCH;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
-    // prefetch the first input
-    tile_prefetch<M, TZ, PITCH, NT>(tin[0], args.in + (args.codes[0] & 255) * args.in_stride, row0, rows);
-    int cur = args.codes[0] & 255, buf = 0;
+    if constexpr (PREFETCH)
+        tile_prefetch<M, TZ, PITCH, NT>(tin[0], args.in + (args.codes[0] & 255) * args.in_stride, row0, rows);
+    int cur = -1, buf = 0;
     for (int f = 0; f < args.nout; ++f) {
         const int code = args.codes[f];
         const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
-        if (f == 0 || in != cur) {
-            if (f > 0) buf ^= 1;
+        if (in != cur) {
+            if constexpr (PREFETCH) {
+                if (cur >= 0) buf ^= 1;
+                cp_async_wait_all();
+                __syncthreads();   // tile complete and visible; the other buffer is no longer read
+                int nf = f + 1;    // prefetch the next distinct input while this one's outputs are formed
+                while (nf < args.nout && (args.codes[nf] & 255) == in) ++nf;
+                if (nf < args.nout)
+                    tile_prefetch<M, TZ, PITCH, NT>(tin[buf ^ 1], args.in + (args.codes[nf] & 255) * args.in_stride,
+                                                    row0, rows);
+            } else {
+                __syncthreads();   // previous input no longer read
+                tile_load<M, TZ, PITCH, NT>(tin[0], args.in + in * args.in_stride, row0, rows);
+                __syncthreads();
+            }
             cur = in;
-            cp_async_wait_all();
-            __syncthreads();   // tile complete and visible; the other buffer is no longer read
-            // prefetch the next distinct input while this one's outputs are formed
-            int nf = f + 1;
-            while (nf < args.nout && (args.codes[nf] & 255) == in) ++nf;
-            if (nf < args.nout)
-                tile_prefetch<M, TZ, PITCH, NT>(tin[buf ^ 1], args.in + (args.codes[nf] & 255) * args.in_stride,
-                                                row0, rows);
         }
         const float2* colp = tin[buf] + c * PITCH;
         float2 x[E];
@@ -411,7 +420,7 @@ k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
         __syncthreads();
         tile_store<M, TZ, PITCH, NT>(args.out + slot * args.out_stride, tex, row0, rows);
     }
-    cp_async_wait_all();
+    if constexpr (PREFETCH) cp_async_wait_all();
 }
 
 // ------------------------------------------- z pass fused with the shell sums
@@ -575,13 +584,14 @@ struct Launch {
         k_yexp<N, TZC><<<grid, TZC * PC, smem, s>>>(a, g.tw, (float)g.kF);
         return cudaGetLastError();
     }
+    template <bool PF>
     static cudaError_t zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
         const long long rows = (long long)N * N;
         dim3 grid((unsigned)((rows + TZZ - 1) / TZZ));
-        const size_t smem = sizeof(float2) * (N + 3 * (size_t)TZZ * PITCH);
-        cudaError_t e = set_smem(k_zexp<N, TZZ>, smem);
+        const size_t smem = sizeof(float2) * (N + (PF ? 3 : 2) * (size_t)TZZ * PITCH);
+        cudaError_t e = set_smem(k_zexp<N, TZZ, PF>, smem);
         if (e != cudaSuccess) return e;
-        k_zexp<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+        k_zexp<N, TZZ, PF><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
         return cudaGetLastError();
     }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
@@ -622,8 +632,8 @@ struct Launch {
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                                   \
     }                                                                                                      \
     cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
-        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ1>::zexp(g, a, s)                                    \
-                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zexp(g, a, s);                                   \
+        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<true>(g, a, s)                     \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<false>(g, a, s);                   \
     }                                                                                                      \
     int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
     cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band, int nf,       \

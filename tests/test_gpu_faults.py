@@ -1,0 +1,69 @@
+"""Failure handling without faulting a GPU: injected host-side failures
+(GRIDSPT_FAULT_INJECT) must surface as status codes with no leak, leave the
+context usable, and later calls must give correct results."""
+import os
+
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1807_04215_gb300 import _lib  # noqa: E402
+from paper_1807_04215_gb300 import gridspt as g  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def inject(monkeypatch):
+    def set_(v):
+        monkeypatch.setenv("GRIDSPT_FAULT_INJECT", v)
+    yield set_
+    monkeypatch.delenv("GRIDSPT_FAULT_INJECT", raising=False)
+
+
+def test_plan_allocation_failure_reports_nomem_without_leak(inject):
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    inject("plan_alloc")
+    for _ in range(200):
+        with pytest.raises(_lib.GridsptError) as ei:
+            g.Plan(64, 3, 500.0)
+        assert ei.value.status == 3          # GRIDSPT_E_NOMEM
+    os.environ.pop("GRIDSPT_FAULT_INJECT")
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 < 2 << 20            # the first allocation was released each time
+
+
+def test_launch_failure_is_reported_and_recoverable(inject):
+    plan = g.Plan(32, 3, 250.0)
+    d1 = g.make_linear_field(plan, [3])
+    ref = g.run_orders(plan, d1).clone()
+    inject("launch")
+    with pytest.raises(_lib.GridsptError) as ei:
+        g.run_orders(plan, d1)
+    assert ei.value.status == 4              # GRIDSPT_E_CUDA
+    assert "launch" in str(ei.value)
+    os.environ.pop("GRIDSPT_FAULT_INJECT")
+    assert torch.equal(g.run_orders(plan, d1), ref)
+
+
+def test_invalid_arguments_are_rejected_before_any_launch():
+    plan = g.Plan(32, 3, 250.0)
+    d1 = g.make_linear_field(plan, [3])
+    spectra = torch.empty(plan.half_shape(1, 2, 2), dtype=torch.complex64, device="cuda")
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    lib = _lib.load()
+    import ctypes
+    st = lib.gridspt_run_orders(plan.handle, ctypes.c_void_p(d1.data_ptr()), 2, ctypes.c_void_p(spectra.data_ptr()),
+                                ctypes.c_void_p(small.data_ptr()), 16, None)
+    assert st == 1 and b"workspace" in lib.gridspt_last_error()
+    st = lib.gridspt_run_orders(plan.handle, ctypes.c_void_p(d1.data_ptr() + 4), 2,
+                                ctypes.c_void_p(spectra.data_ptr()), ctypes.c_void_p(small.data_ptr()), 16, None)
+    assert st == 1 and b"aligned" in lib.gridspt_last_error()
+    kF = 6.283185307179586 / 250.0
+    with pytest.raises(_lib.GridsptError):
+        g.power(plan, d1[0], d1[0], [kF * i for i in range(40)])     # above the Nyquist wavenumber
+    with pytest.raises(_lib.GridsptError):
+        g.bispectrum(plan, d1[0], d1[0], [kF * i for i in range(20)])  # shells beyond 2 k_Ny / 3
