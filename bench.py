@@ -30,9 +30,10 @@ METRIC = "Mcells*orders/s to 5th order at 512^3 FP32"
 UNIT = "Mcells*orders/s"
 N_GRID, BOX, N_MAX = 512, 2000.0, 5
 FALLBACK_HBM_GBS = 6800.0
-# bytes per launch from the last ncu capture of the dominant kernel (None until taken
-# for the current kernel source)
-NCU_TRAFFIC = {}
+# DRAM traffic / algorithmic bytes measured by ncu for the kernels as they stand
+# (profiles/k_xexp_k_yexp_k_zexp_c2r-512.md: 512^3, one field per launch);
+# traffic per launch is reported as this ratio times the launch's algorithmic bytes
+NCU_TRAFFIC_RATIO = {"z_expand": 0.969, "y_expand": 0.969, "x_expand": 0.966}
 
 
 def log_edges(lo, hi, nb):
@@ -245,6 +246,17 @@ def run_gpu(args, rank, world):
         e2e_step()
     e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, dist, "cuda")
 
+    # the same recursion (all B realisations) captured once as a CUDA graph and replayed
+    graph = g.Batch([plan], [d1], spectra=[spectra], wss=[ws])
+    graph.launch()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        graph.launch()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = ev0.elapsed_time(ev1) / args.steps
+    graph.close()
     mixed = mixed_batch(args) if rank == 0 and not args.quick else None
     emu = emulator_section(args) if rank == 0 and not args.quick else None
     if rank != 0:
@@ -271,7 +283,9 @@ def run_gpu(args, rank, world):
                    "l2": "inputs larger than L2 (512 MiB fields), no flush", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": NCU_TRAFFIC.get(kname)},
+                     "traffic": (round(NCU_TRAFFIC_RATIO[kname] * kbytes / nl / 1e9, 3) if kname in NCU_TRAFFIC_RATIO
+                                 else None),
+                     "traffic_unit": "GB per launch", "algorithmic_per_launch": round(kbytes / nl / 1e9, 3)},
         "recursion_ms_per_realisation": round(sum(prof[k][1] for k in rec_kinds if k in prof) / args.steps / B, 3),
         "kernels": breakdown,
         "clocks": clk,
@@ -280,6 +294,9 @@ def run_gpu(args, rank, world):
                 "ms_per_step": e2e_ms, "path": "delta_1(k) from pinned host -> run_orders -> estimators -> host"},
         "cpu_baseline": cb,
         "autotune": tuning,
+        "recursion_graph": {"ms_per_launch": round(graph_ms, 3), "realisations": B,
+                            "value": round(B * N ** 3 * (N_MAX - 1) / graph_ms / 1e3, 1),
+                            "unit": "Mcells*orders/s (orders 2..5, one graph launch, IC excluded)"},
         "mixed_batch": mixed,
         "emulator": emu,
     }
