@@ -205,13 +205,14 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
 
 /* Autotuner for the transform passes (not part of the paper's method). Each
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
- * 4 contiguous-axis forward pass) has two tile-width variants for N >= 128
- * (identical for smaller N). gridspt_autotune times both variants of every
+ * 4 contiguous-axis forward pass) has two variants for N >= 128 (identical for
+ * smaller N); the y expansion has a third, TMA-staged one (N >= 128). gridspt_autotune times both variants of every
  * pass on `scratch` (device, >= gridspt_autotune_scratch_size bytes, contents
  * overwritten) with CUDA events on `stream`, keeps the faster one in the plan
  * and writes the choices to choices_out (host int32[5], may be NULL). It
  * synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning store and
- * read the choices (each 0 or 1), e.g. from a cache kept by the caller.
+ * read the choices (0 or 1; 0..2 for the y expansion), e.g. from a cache kept
+ * by the caller.
  * Results are bitwise identical for both variants: they only change how
  * columns and rows are grouped into thread blocks. */
 gridspt_status gridspt_autotune_scratch_size(gridspt_plan plan, size_t* bytes);
@@ -275,6 +276,19 @@ typedef struct {
 } gridspt_kernel_stat;
 gridspt_status gridspt_profile_begin(void);
 gridspt_status gridspt_profile_end(gridspt_kernel_stat* stats, int32_t capacity, int32_t* count);
+
+/* Device-side status: synchronises `stream` and returns GRIDSPT_E_TIMEOUT if a
+ * bounded device-side wait (the mbarrier waits of the TMA-staged passes) gave
+ * up since the last check, in which case the results of those calls are
+ * invalid; the status is then reset. GRIDSPT_OK otherwise. */
+gridspt_status gridspt_check(gridspt_plan plan, gridspt_stream stream);
+
+/* Failure-detection self-test (not part of the paper's method): launches one
+ * block that waits, with the same bounded wait as the TMA-staged passes, on a
+ * barrier that is never completed. The wait gives up (about 1 ms), the kernel
+ * records the timeout and returns; the next gridspt_check reports
+ * GRIDSPT_E_TIMEOUT. Nothing faults or hangs. */
+gridspt_status gridspt_selftest_bounded_wait(gridspt_plan plan, gridspt_stream stream);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* gridspt_last_error(void);

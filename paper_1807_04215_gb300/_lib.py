@@ -66,6 +66,8 @@ SIGNATURES = {
                                    ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    c_void_p]),
     "gridspt_mlp_convert": (c_int32, [c_void_p, c_void_p, c_int32, ctypes.c_int64, c_void_p]),
+    "gridspt_check": (c_int32, [c_void_p, c_void_p]),
+    "gridspt_selftest_bounded_wait": (c_int32, [c_void_p, c_void_p]),
     "gridspt_profile_begin": (c_int32, []),
     "gridspt_profile_end": (c_int32, [ctypes.POINTER(GridsptKernelStat), c_int32, ctypes.POINTER(c_int32)]),
     "gridspt_last_error": (ctypes.c_char_p, []),

@@ -30,6 +30,7 @@ struct gridspt_plan_s {
     long long pb_top = -1;  // cache of the last power-launch byte count (profiling only)
     double pb_modes = 0.0;
     double* j3 = nullptr;   // device [kMaxBins]: sum_x J^3 per bispectrum shell (data independent)
+    int* status = nullptr;  // device status word (bounded waits that gave up)
     int j3_nb = 0;          // shells the cache holds (0: empty) and their thresholds
     int j3_thr[kMaxBins + 1] = {};
 };
@@ -279,12 +280,17 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     }
     e = cudaMalloc(&p->tw, sizeof(float2) * N);
     if (e != cudaSuccess) { delete p; return fail(GRIDSPT_E_NOMEM, "twiddle table: %s", cudaGetErrorString(e)); }
-    e = fault_inject("plan_alloc") ? cudaErrorMemoryAllocation : cudaMalloc(&p->j3, sizeof(double) * kMaxBins);
+    e = fault_inject("plan_alloc") ? cudaErrorMemoryAllocation
+                                   : cudaMalloc(&p->j3, sizeof(double) * kMaxBins + sizeof(int) * 4);
     if (e != cudaSuccess) {
         cudaFree(p->tw);
         delete p;
         return fail(GRIDSPT_E_NOMEM, "shell cache: %s", cudaGetErrorString(e));
     }
+    p->status = reinterpret_cast<int*>(p->j3 + kMaxBins);
+    p->geo.status = p->status;
+    e = cudaMemset(p->status, 0, sizeof(int));
+    if (e != cudaSuccess) { cudaFree(p->tw); cudaFree(p->j3); delete p; return cuda_fail(e, "status word"); }
     e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(p->tw); cudaFree(p->j3); delete p; return cuda_fail(e, "twiddle upload"); }
     p->geo.tw = p->tw;
@@ -647,7 +653,8 @@ gridspt_status gridspt_set_tuning(gridspt_plan p, const int32_t* choices) {
     g_err[0] = 0;
     if (check_plan(p) || !choices) return fail(GRIDSPT_E_INVALID, "plan/choices is NULL");
     for (int i = 0; i < TV_COUNT; ++i)
-        if (choices[i] != 0 && choices[i] != 1) return fail(GRIDSPT_E_INVALID, "choice %d must be 0 or 1", i);
+        if (choices[i] < 0 || choices[i] >= kTuneVariants[i])
+            return fail(GRIDSPT_E_INVALID, "choice %d must be in [0, %d)", i, kTuneVariants[i]);
     for (int i = 0; i < TV_COUNT; ++i) p->geo.var[i] = choices[i];
     return GRIDSPT_OK;
 }
@@ -713,10 +720,14 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
     for (int pass = 0; pass < TV_COUNT && e == cudaSuccess; ++pass) {
         float tbest = 0.f;
         best[pass] = 0;
-        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        for (int v = 0; v < kTuneVariants[pass] && e == cudaSuccess; ++v) {
             Geo g = p->geo;
             g.var[pass] = v;
             e = run(g, pass);   // warm-up
+            if (e == cudaErrorNotSupported) {   // variant not built for this size
+                e = cudaSuccess;
+                continue;
+            }
             if (e == cudaSuccess) e = cudaEventRecord(a, s);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run(g, pass);
             if (e == cudaSuccess) e = cudaEventRecord(b, s);
@@ -736,6 +747,27 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
         p->geo.var[i] = best[i];
         if (choices_out) choices_out[i] = best[i];
     }
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_check(gridspt_plan p, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "check: stream synchronize");
+    int st = 0;
+    CK(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost), "check: read status");
+    if (st) {
+        CK(cudaMemset(p->status, 0, sizeof(int)), "check: reset status");
+        return fail(GRIDSPT_E_TIMEOUT, "a bounded device-side wait gave up (status %d); results of the calls since "
+                                       "the last check are invalid", st);
+    }
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_selftest_bounded_wait(gridspt_plan p, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    CK(launch_wait_selftest(p->status, (cudaStream_t)stream), "bounded-wait self-test");
     return GRIDSPT_OK;
 }
 

@@ -21,7 +21,11 @@ struct Geo {
     double kF;              // 2 pi / L
     const float2* tw;       // device table e^{+2 pi i j / N}, j < N (FP32 from FP64)
     int var[TV_COUNT];      // tile variant per transform pass
+    int* status;            // device status word: set to 1 when a bounded wait gives up
 };
+
+// number of tile variants per pass (the autotuner times each)
+constexpr int kTuneVariants[TV_COUNT] = {2, 2, 3, 2, 2};
 
 // Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every
 // derived field is c * kx^a * ky^b * kz^g * src(k) with src in {delta, theta,
@@ -96,6 +100,9 @@ struct BinSpec {
 };
 
 cudaError_t launch_ic(const Geo& g, const IcArgs& a, cudaStream_t s);
+// One block waits on an mbarrier that nothing completes; the bounded wait gives
+// up and sets *status (exercises the timeout path without hanging the GPU).
+cudaError_t launch_wait_selftest(int* status, cudaStream_t s);
 cudaError_t launch_xexp(const Geo& g, const XExpArgs& a, cudaStream_t s);
 cudaError_t launch_yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);
 cudaError_t launch_zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);

@@ -18,6 +18,8 @@
 // packed sequence z[m] = x[2m] + i x[2m+1]; the Nyquist coefficient X[N/2] is
 // zero in every spectrum of this library and is not stored.
 #pragma once
+#include <cuda.h>
+
 #include "fft_core.cuh"
 #include "gridspt_internal.h"
 
@@ -423,6 +425,126 @@ k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
     if constexpr (PREFETCH) cp_async_wait_all();
 }
 
+// ------------------------------------------------- TMA-staged y expansion
+// Same computation as k_yexp, but each input column tile (all N rows of TZ
+// adjacent kz columns of one x plane) is copied into shared memory by the
+// tensor-memory accelerator (cp.async.bulk.tensor, 4D map over kz, ky, x and
+// field), completion tracked by an mbarrier, while the previous input's
+// outputs are transformed. The tile being consumed is read into registers and
+// then serves as the transform's exchange buffer. Every wait is bounded: on
+// timeout the kernel sets *status and continues (results are then invalid and
+// gridspt_check reports GRIDSPT_E_TIMEOUT); it never traps or spins forever.
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(bar)), "r"(bytes) : "memory");
+}
+// true when the phase with the given parity has completed; bounded
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"((unsigned)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// rows per TMA box: the largest divisor of N not above 256 (a box dimension is at most 256)
+__host__ __device__ constexpr int tma_rows(int N) { return N <= 256 ? N : (N % 256 == 0 ? 256 : N / 2 <= 256 ? N / 2 : 192); }
+
+template <int N, int TZ>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC, (TZ * Cfg<N>::PC <= 512) ? 2 : 1)
+k_yexp_tma(YZExpArgs args, const __grid_constant__ CUtensorMap tmap, const float2* __restrict__ twg, float kF,
+           int* __restrict__ status) {
+    constexpr int M = N / 2, E = fft_elems(N), P = N / E;
+    constexpr int BR = tma_rows(N);
+    static_assert(N % BR == 0 && BR <= 256, "TMA box rows must divide N");
+    constexpr unsigned TILE_BYTES = (unsigned)N * TZ * sizeof(float2);
+    extern __shared__ unsigned char smraw[];
+    // tiles start on a 1024-byte boundary (TMA destinations need at least 128)
+    const unsigned base_off = (1024u - ((unsigned)__cvta_generic_to_shared(smraw) & 1023u)) & 1023u;
+    unsigned char* smb = smraw + base_off;
+    float2* tile[2] = {reinterpret_cast<float2*>(smb), reinterpret_cast<float2*>(smb + TILE_BYTES)};
+    float2* tw = reinterpret_cast<float2*>(smb + 2 * TILE_BYTES);
+    __shared__ uint64_t bar[2];
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    const int kz0 = blockIdx.x * TZ;
+    const int xr = blockIdx.y;
+    load_table(tw, twg, N);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    auto issue = [&](int b, int in) {   // thread 0 only
+        mbar_expect_tx(&bar[b], TILE_BYTES);
+#pragma unroll
+        for (int r = 0; r < N / BR; ++r) tma_load_4d(tile[b] + r * BR * TZ, &tmap, kz0, r * BR, xr, in, &bar[b]);
+    };
+    if (tid == 0) issue(0, args.codes[0] & 255);
+    unsigned phase[2] = {0u, 0u};
+    int pending[2] = {1, 0};
+    int buf = 0, cur = -1;
+    bool ok = true;
+    constexpr long long estride = (long long)M;
+    const long long colofs = (long long)xr * N * M + kz0 + c;
+    float2 xin[E];
+    for (int f = 0; f < args.nout; ++f) {
+        const int code = args.codes[f];
+        const int in = code & 255, pb = (code >> 8) & 3, slot = code >> 16;
+        if (in != cur) {
+            if (cur >= 0) buf ^= 1;
+            ok = mbar_wait(&bar[buf], phase[buf]) && ok;
+            phase[buf] ^= 1u;
+            pending[buf] = 0;
+#pragma unroll
+            for (int i = 0; i < E; ++i) xin[i] = tile[buf][(p + P * i) * TZ + c];
+            fence_proxy_async();     // generic-proxy use of the other tile ends before the TMA refills it
+            __syncthreads();
+            int nf = f + 1;
+            while (nf < args.nout && (args.codes[nf] & 255) == in) ++nf;
+            if (nf < args.nout) {
+                if (tid == 0) issue(buf ^ 1, args.codes[nf] & 255);
+                pending[buf ^ 1] = 1;
+            }
+            cur = in;
+        }
+        float2 y[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float ky = kF * (float)signed_idx(p + P * i, N);
+            y[i] = pb == 0 ? xin[i] : cscale(xin[i], pb == 1 ? ky : ky * ky);
+        }
+        fft_column<N, +1, N>(y, p, tile[buf] + c, TZ, tw);
+        float2* o = args.out + slot * args.out_stride + colofs;
+#pragma unroll
+        for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
+    }
+    // never leave with a copy in flight into this block's shared memory
+    for (int b = 0; b < 2; ++b)
+        if (pending[b]) ok = mbar_wait(&bar[b], phase[b]) && ok;
+    if (!ok && tid == 0) atomicExch(status, 1);
+}
+
 // ------------------------------------------- z pass fused with the shell sums
 // Bispectrum estimator, one shell (Sec. III.B.1, Eq. bk_tree, FFT shell
 // estimator): the three xy-fields I_a, I_b, J (nonzero only for kz < band)
@@ -520,6 +642,10 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
 }
 
 // ------------------------------------------------------------- launchers
+// cuTensorMapEncodeTiled through the runtime's driver entry point (k_tma_host.cpp)
+cudaError_t encode_tensor_map(CUtensorMap* map, void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                              const cuuint32_t* box, const cuuint32_t* elem_strides);
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024)
@@ -594,6 +720,32 @@ struct Launch {
         k_zexp<N, TZZ, PF><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
         return cudaGetLastError();
     }
+    // TMA-staged y expansion: 8-column tiles, two tile buffers per block
+    static cudaError_t yexp_tma(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
+        constexpr int TZ = 8;
+        constexpr int BR = tma_rows(N);
+        if (N < 128 || M % TZ != 0) return cudaErrorNotSupported;
+        int nin = 0;
+        for (int f = 0; f < a.nout; ++f) nin = (a.codes[f] & 255) + 1 > nin ? (a.codes[f] & 255) + 1 : nin;
+        CUtensorMap map;
+        // dims: kz (M), ky (N), x (N), field (nin); element = 8 bytes (one float2)
+        const cuuint64_t dims[4] = {(cuuint64_t)M, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)nin};
+        const cuuint64_t strides[3] = {(cuuint64_t)M * 8, (cuuint64_t)N * M * 8, (cuuint64_t)a.in_stride * 8};
+        const cuuint32_t box[4] = {(cuuint32_t)TZ, (cuuint32_t)BR, 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        // host-side checks of the TMA rules: 16-byte aligned base and strides, inner box
+        // extent a multiple of 16 bytes, box rows <= 256; every kz offset used is a
+        // multiple of TZ = 8 columns (64 bytes)
+        if ((reinterpret_cast<uintptr_t>(a.in) & 15) || (strides[2] & 15) || (TZ * 8) % 16 || BR > 256)
+            return cudaErrorInvalidValue;
+        cudaError_t e = encode_tensor_map(&map, const_cast<float2*>(a.in), dims, strides, box, estr);
+        if (e != cudaSuccess) return e;
+        const size_t smem = 2 * (size_t)N * TZ * sizeof(float2) + sizeof(float2) * N + 1024;   // + alignment slack
+        if ((e = set_smem(k_yexp_tma<N, TZ>, smem)) != cudaSuccess) return e;
+        dim3 grid(M / TZ, N);
+        k_yexp_tma<N, TZ><<<grid, TZ * PC, smem, s>>>(a, map, g.tw, (float)g.kF, g.status);
+        return cudaGetLastError();
+    }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
     static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, double* partial,
                               cudaStream_t s) {
@@ -628,8 +780,9 @@ struct Launch {
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::xexp(g, a, s);                                   \
     }                                                                                                      \
     cudaError_t transform_yexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
-        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::yexp(g, a, s)                                    \
-                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                                   \
+        if (v == 2 && N >= 128 && a.band <= 0) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp_tma(g, a, s); \
+        return v == 1 ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::yexp(g, a, s)                               \
+                      : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                              \
     }                                                                                                      \
     cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
         return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<true>(g, a, s)                     \

@@ -152,6 +152,11 @@ class Batch:
             pass
 
 
+def check(plan):
+    """gridspt_check: raises GridsptError (status 5) if a bounded device wait gave up."""
+    _lib.check("gridspt_check", plan.lib.gridspt_check(plan.handle, _stream()))
+
+
 def autotune(plan, scratch=None):
     """Time both tile variants of every transform pass and keep the faster;
     returns the choices [column pass, x, y, z expansion, z forward]."""

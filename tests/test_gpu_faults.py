@@ -67,3 +67,22 @@ def test_invalid_arguments_are_rejected_before_any_launch():
         g.power(plan, d1[0], d1[0], [kF * i for i in range(40)])     # above the Nyquist wavenumber
     with pytest.raises(_lib.GridsptError):
         g.bispectrum(plan, d1[0], d1[0], [kF * i for i in range(20)])  # shells beyond 2 k_Ny / 3
+
+
+def test_bounded_device_wait_reports_timeout_and_context_stays_usable():
+    """A device wait that nothing completes gives up after its limit, the status
+    word reports it (GRIDSPT_E_TIMEOUT), and the next calls work."""
+    import ctypes
+    plan = g.Plan(32, 3, 250.0)
+    g.check(plan)
+    lib = _lib.load()
+    assert lib.gridspt_selftest_bounded_wait(plan.handle, None) == 0
+    with pytest.raises(_lib.GridsptError) as ei:
+        g.check(plan)
+    assert ei.value.status == 5
+    g.check(plan)                       # status was reset
+    d1 = g.make_linear_field(plan, [3])
+    a = g.run_orders(plan, d1).clone()
+    assert torch.equal(g.run_orders(plan, d1), a)
+    g.check(plan)
+    del ctypes
