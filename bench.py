@@ -201,7 +201,7 @@ def run_gpu(args, rank, world):
         g.run_orders(plan, d1, spectra=spectra, ws=ws)
         estimators()
 
-    tuning = g.autotune(plan, scratch=ws[: 4 * 4 * N ** 3])
+    tuning = g.autotune(plan, scratch=ws)
 
     for _ in range(args.warmup):
         step()

@@ -142,10 +142,17 @@ long long field_floats(const gridspt_plan_s* p) { return (long long)p->geo.N * p
 long long field_c(const gridspt_plan_s* p) { return (long long)p->geo.N * p->geo.N * p->geo.M; }
 
 int order_base(int m) { return m == 1 ? 0 : 13 + 17 * (m - 2); }
-int total_derived(int n_max) { return n_max >= 2 ? order_base(n_max) : 0; }
-// scratch of one derivative expansion: 7 x-fields + 12 xy-fields
+// Accumulate-ahead workspace (fields of 4 N^3 bytes): the real derived fields
+// of the orders that later pairs still need (2m <= n_max), two accumulator
+// fields (A, B) per target order n >= 4, then the expansion scratch
+// (7 x-fields + 12 xy-fields).
 constexpr int kExpScratch = 7 + 12;
-int workspace_fields(int n_max) { return n_max >= 2 ? total_derived(n_max) + kExpScratch : 0; }
+int stored_orders(int n_max) { return n_max / 2; }
+int total_derived(int n_max) { return n_max >= 2 ? order_base(stored_orders(n_max) + 1) : 0; }
+int acc_base(int n_max) { return total_derived(n_max); }
+int n_acc(int n_max) { return n_max >= 4 ? 2 * (n_max - 3) : 0; }
+int scratch_base(int n_max) { return acc_base(n_max) + n_acc(n_max); }
+int workspace_fields(int n_max) { return n_max >= 2 ? scratch_base(n_max) + kExpScratch : 0; }
 
 // s2 threshold: smallest integer t >= 0 with kF * sqrt(t) >= e (FP64), so that
 // "t <= |s|^2" is exactly the FP64 test "e <= kF sqrt(|s|^2)".
@@ -352,47 +359,8 @@ gridspt_status gridspt_make_linear_field(gridspt_plan p, const gridspt_cosmo* c,
 
 namespace {
 
-// Derived fields of order m from its spectra (Sec. II.C steps (2)/(5)),
-// written to ws at the order's slot, through the factorised x, y and z
-// expansion passes. With fwd, the spectra buffers hold the y-transformed
-// product output and the x pass first completes the forward transform
-// (writing delta_m(k), theta_m(k) in place).
-//
-// Order m >= 2, 17 real fields in slot order [delta, theta, d delta (3),
-// d theta (3), u (3), d_a u_b (xx, yy, zz, xy, xz, yz)], phi = theta / k^2:
-//   x-fields: X0 delta, X1 kx delta, X2 theta, X3 kx theta, X4 phi, X5 kx phi, X6 kx^2 phi
-//   xy-fields: Y0 X0, Y1 ky X0, Y2 X1, Y3 X2, Y4 ky X2, Y5 X3, Y6 X4, Y7 ky X4, Y8 ky^2 X4,
-//              Y9 X5, Y10 ky X5, Y11 X6
-//   real: delta = Y0, d_z delta = i kz Y0, d_y delta = i Y1, d_x delta = i Y2, theta = Y3,
-//         d_z theta = i kz Y3, d_y theta = i Y4, d_x theta = i Y5, u_z = -i kz Y6,
-//         d_z u_z = kz^2 Y6, u_y = -i Y7, d_y u_z = kz Y7, d_y u_y = Y8, u_x = -i Y9,
-//         d_x u_z = kz Y9, d_x u_y = Y10, d_x u_x = Y11.
-// Order 1 (theta = delta), 13 fields [delta, d delta (3), u (3), d_a u_b (6)]:
-//   x-fields: X0 delta, X1 kx delta, X2 phi, X3 kx phi, X4 kx^2 phi
-//   xy-fields: Y0 X0, Y1 ky X0, Y2 X1, Y3 X2, Y4 ky X2, Y5 ky^2 X2, Y6 X3, Y7 ky X3, Y8 X4
-gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* tk, float* ws,
-                            bool fwd, cudaStream_t s) {
-    const long long F = field_c(p);
-    const double fb = 4.0 * (double)field_floats(p);  // bytes of one field
-    float2* real = reinterpret_cast<float2*>(ws + (long long)order_base(m) * field_floats(p));
-    float2* xs = reinterpret_cast<float2*>(ws + (long long)total_derived(p->d.n_max) * field_floats(p));
-    float2* ys = xs + 7 * F;
-    XExpArgs xa{};
-    xa.src0 = dk;
-    xa.src1 = tk;
-    xa.out = xs;
-    xa.out_stride = F;
-    xa.fwd_first = fwd ? 1 : 0;
-    xa.s2_nl = p->s2_nl;
-    YZExpArgs ya{}, za{};
-    ya.in = xs;
-    ya.in_stride = F;
-    ya.out = ys;
-    ya.out_stride = F;
-    za.in = ys;
-    za.in_stride = F;
-    za.out = real;
-    za.out_stride = F;
+// The x-, y- and z-expansion output lists of order m (see derive_order).
+void expansion_codes(int m, XExpArgs& xa, YZExpArgs& ya, YZExpArgs& za) {
     const int I = 1, NI = 2;  // z-pass constants i and -i
     if (m == 1) {
         const int xc[5] = {x_code(XK_POW, 0, XS_DELTA), x_code(XK_POW, 1, XS_DELTA), x_code(XK_POW, 0, XS_PHI),
@@ -428,12 +396,158 @@ gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* 
         for (int i = 0; i < 12; ++i) ya.codes[i] = yc[i];
         for (int i = 0; i < 17; ++i) za.codes[i] = zc[i];
     }
+}
+
+// Recursion coefficients of order n times N^-3: (delta_n, theta_n) =
+// c_n [(n + 1/2) A + B, 3/2 A + n B] / N^3 (Eq. recursion_formula).
+void recursion_coefs(const gridspt_plan_s* p, int n, float* cdA, float* cdB, float* ctA, float* ctB) {
+    const double inv_cells = 1.0 / (double)field_floats(p);
+    const double c = 2.0 / ((2.0 * n + 3.0) * (n - 1.0));
+    *cdA = (float)(c * (n + 0.5) * inv_cells);
+    *cdB = (float)(c * inv_cells);
+    *ctA = (float)(c * 1.5 * inv_cells);
+    *ctB = (float)(c * n * inv_cells);
+}
+
+// Partner fields of produced slot s (order m >= 2, 17 slots) in the stored
+// order j (13 slots for j = 1, where theta_1 = delta_1, else 17), with the
+// coefficients of both ordered pairs (m, j) and (j, m) in A and B.
+void pair_table(int j, PairTarget& T) {
+    auto f = [&](int slot17) {   // stored field index of canonical slot
+        if (j >= 2) return slot17;
+        if (slot17 <= 1) return 0;                 // delta, theta
+        if (slot17 <= 4) return 1 + (slot17 - 2);  // grad delta
+        if (slot17 <= 7) return 1 + (slot17 - 5);  // grad theta = grad delta
+        if (slot17 <= 10) return 4 + (slot17 - 8); // u
+        return 7 + (slot17 - 11);                  // d_a u_b
+    };
+    for (int sl = 0; sl < 17; ++sl) {
+        T.pcount[sl] = 0;
+        auto add = [&](int slot17, float ca, float cb) {
+            const int fi = f(slot17);
+            for (int q = 0; q < T.pcount[sl]; ++q)
+                if (T.pfield[sl][q] == fi) {   // aliased partner: merge coefficients
+                    T.pcoef_a[sl][q] += ca;
+                    T.pcoef_b[sl][q] += cb;
+                    return;
+                }
+            T.pfield[sl][T.pcount[sl]] = fi;
+            T.pcoef_a[sl][T.pcount[sl]] = ca;
+            T.pcoef_b[sl][T.pcount[sl]] = cb;
+            ++T.pcount[sl];
+        };
+        if (sl == 0) add(1, 1.f, 0.f);                       // delta_m theta_j
+        else if (sl == 1) add(0, 1.f, 0.f);                  // delta_j theta_m
+        else if (sl <= 4) add(8 + (sl - 2), 1.f, 0.f);       // grad delta_m . u_j
+        else if (sl <= 7) add(8 + (sl - 5), 0.f, 1.f);       // u_j . grad theta_m
+        else if (sl <= 10) {                                 // grad delta_j . u_m, u_m . grad theta_j
+            add(2 + (sl - 8), 1.f, 0.f);
+            add(5 + (sl - 8), 0.f, 1.f);
+        } else if (sl <= 13) add(sl, 0.f, 2.f);              // diagonal d_a u_a, both orders
+        else add(sl, 0.f, 4.f);                              // off-diagonal (symmetric) x both orders
+    }
+}
+
+// z pass of order m fused with the pair products (m, j), j < m, m + j <= n_max,
+// for the targets n' = m + j >= start. Stores the order's real fields when a
+// later order needs them (2m <= n_max). More than two targets are split over
+// several launches (the z expansion is then repeated).
+gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, float* ws, int start,
+                          const std::vector<float2*>& spec_delta, cudaStream_t s) {
+    const int n_max = p->d.n_max;
+    const long long cells = field_floats(p);
+    const double fb = 4.0 * (double)cells;
+    std::vector<int> js;
+    for (int j = 1; j < m && m + j <= n_max; ++j)
+        if (m + j >= start) js.push_back(j);
+    const bool store = 2 * m <= n_max;
+    size_t first = 0;
+    do {
+        ZPairArgs a{};
+        a.z = za;
+        a.cells = cells;
+        a.store = (store && first == 0) ? ws + (long long)order_base(m) * cells : nullptr;
+        a.ntargets = 0;
+        double bytes = fb * za.nout * (a.store ? 1 : 0) + fb * (m == 1 ? 9 : 12);   // stores + xy-field inputs
+        for (size_t q = first; q < js.size() && a.ntargets < kMaxPairTargets; ++q, ++first) {
+            const int j = js[q], n = m + j;
+            PairTarget& T = a.t[a.ntargets++];
+            T.partner = ws + (long long)order_base(j) * cells;
+            pair_table(j, T);
+            // the first contribution to target n comes from order ceil(n / 2)
+            // (the diagonal pair for even n), every later one reads the partial sums
+            const int first_m = (n + 1) / 2;
+            float* acc = ws + (long long)(acc_base(n_max) + 2 * (n - 4)) * cells;
+            if (first_m < m) {
+                T.acc_in_a = acc;
+                T.acc_in_b = acc + cells;
+            }
+            if (j == 1) {   // last pair of target n: write delta_n, theta_n
+                T.out_a = reinterpret_cast<float*>(spec_delta[n]);
+                T.out_b = reinterpret_cast<float*>(spec_delta[n] + field_c(p));
+                recursion_coefs(p, n, &T.ca0, &T.ca1, &T.cb0, &T.cb1);
+            } else {
+                T.out_a = acc;
+                T.out_b = acc + cells;
+                T.ca0 = 1.f;
+                T.ca1 = 0.f;
+                T.cb0 = 0.f;
+                T.cb1 = 1.f;
+            }
+            bytes += fb * (j == 1 ? 13 : 17) + fb * 2 + (T.acc_in_a ? fb * 2 : 0);
+        }
+        if (!a.store && a.ntargets == 0) break;
+        CKP(PK_ZEXP, bytes, s, launch_zexp_pairs(p->geo, a, s), "z expansion and pair products");
+    } while (first < js.size());
+    return GRIDSPT_OK;
+}
+
+// Derived fields of order m from its spectra (Sec. II.C steps (2)/(5)),
+// written to ws at the order's slot, through the factorised x, y and z
+// expansion passes. With fwd, the spectra buffers hold the y-transformed
+// product output and the x pass first completes the forward transform
+// (writing delta_m(k), theta_m(k) in place).
+//
+// Order m >= 2, 17 real fields in slot order [delta, theta, d delta (3),
+// d theta (3), u (3), d_a u_b (xx, yy, zz, xy, xz, yz)], phi = theta / k^2:
+//   x-fields: X0 delta, X1 kx delta, X2 theta, X3 kx theta, X4 phi, X5 kx phi, X6 kx^2 phi
+//   xy-fields: Y0 X0, Y1 ky X0, Y2 X1, Y3 X2, Y4 ky X2, Y5 X3, Y6 X4, Y7 ky X4, Y8 ky^2 X4,
+//              Y9 X5, Y10 ky X5, Y11 X6
+//   real: delta = Y0, d_z delta = i kz Y0, d_y delta = i Y1, d_x delta = i Y2, theta = Y3,
+//         d_z theta = i kz Y3, d_y theta = i Y4, d_x theta = i Y5, u_z = -i kz Y6,
+//         d_z u_z = kz^2 Y6, u_y = -i Y7, d_y u_z = kz Y7, d_y u_y = Y8, u_x = -i Y9,
+//         d_x u_z = kz Y9, d_x u_y = Y10, d_x u_x = Y11.
+// Order 1 (theta = delta), 13 fields [delta, d delta (3), u (3), d_a u_b (6)]:
+//   x-fields: X0 delta, X1 kx delta, X2 phi, X3 kx phi, X4 kx^2 phi
+//   xy-fields: Y0 X0, Y1 ky X0, Y2 X1, Y3 X2, Y4 ky X2, Y5 ky^2 X2, Y6 X3, Y7 ky X3, Y8 X4
+gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* tk, float* ws, bool fwd,
+                            int start, const std::vector<float2*>& spec_delta, cudaStream_t s) {
+    const long long F = field_c(p);
+    const double fb = 4.0 * (double)field_floats(p);  // bytes of one field
+    float2* xs = reinterpret_cast<float2*>(ws + (long long)scratch_base(p->d.n_max) * field_floats(p));
+    float2* ys = xs + 7 * F;
+    XExpArgs xa{};
+    xa.src0 = dk;
+    xa.src1 = tk;
+    xa.out = xs;
+    xa.out_stride = F;
+    xa.fwd_first = fwd ? 1 : 0;
+    xa.s2_nl = p->s2_nl;
+    YZExpArgs ya{}, za{};
+    ya.in = xs;
+    ya.in_stride = F;
+    ya.out = ys;
+    ya.out_stride = F;
+    za.in = ys;
+    za.in_stride = F;
+    za.out = nullptr;
+    za.out_stride = F;
+    expansion_codes(m, xa, ya, za);
     const int nin = m == 1 ? 1 : 2;
     CKP(fwd ? PK_XEXP_FWD : PK_XEXP, fb * (fwd ? 2 * nin + xa.nout : nin + xa.nout), s,
         launch_xexp(p->geo, xa, s), "x expansion");
     CKP(PK_YEXP, fb * (xa.nout + ya.nout), s, launch_yexp(p->geo, ya, s), "y expansion");
-    CKP(PK_ZEXP, fb * (ya.nout + za.nout), s, launch_zexp(p->geo, za, s), "z expansion");
-    return GRIDSPT_OK;
+    return zexp_pairs(p, m, za, ws, start, spec_delta, s);
 }
 
 // Backward transform of `count` fields in place (or in -> out): x, y, z passes
@@ -498,39 +612,53 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
     if (gridspt_status st = set_device(p)) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const long long F = field_c(p);
-    const double inv_cells = 1.0 / (double)field_floats(p);
     float* w = static_cast<float*>(ws);
     for (int b = 0; b < p->d.batch; ++b) {
         float2* d1 = const_cast<float2*>(static_cast<const float2*>(delta1_k)) + (long long)b * F;
         auto spec = [&](int n, int which) {
             return static_cast<float2*>(spectra) + ((long long)(b * (n_max - 1) + (n - 2)) * 2 + which) * F;
         };
-        // derived fields of the orders below start_order, from stored spectra
-        if (gridspt_status st = derive_order(p, 1, d1, d1, w, false, s)) return st;
-        for (int m = 2; m < start_order; ++m)
-            if (gridspt_status st = derive_order(p, m, spec(m, 0), spec(m, 1), w, false, s)) return st;
-        for (int n = start_order; n <= n_max; ++n) {
-            ProductArgs pa{};
-            pa.ws = w;
-            pa.cells = field_floats(p);
-            for (int m = 1; m <= kMaxOrder; ++m) pa.base[m] = order_base(m);
-            pa.n = n;
-            pa.out_delta = reinterpret_cast<float*>(spec(n, 0));
-            pa.out_theta = reinterpret_cast<float*>(spec(n, 1));
-            const double c = 2.0 / ((2.0 * n + 3.0) * (n - 1.0));
-            pa.cdA = (float)(c * (n + 0.5) * inv_cells);
-            pa.cdB = (float)(c * inv_cells);
-            pa.ctA = (float)(c * 1.5 * inv_cells);
-            pa.ctB = (float)(c * n * inv_cells);
-            const double fb = 4.0 * (double)field_floats(p);
-            CKP(PK_PRODUCT, fb * (order_base(n) + 2), s, launch_product(p->geo, pa, s), "product launch");
-            CKP(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, spec(n, 0), spec(n, 0), F, 2, 1.0f, s), "z r2c");
-            CKP(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, spec(n, 0), F, 2, 1, 0, -1, s), "y pass fwd");
-            if (n < n_max) {
-                if (gridspt_status st = derive_order(p, n, spec(n, 0), spec(n, 1), w, true, s)) return st;
-            } else {
-                CKP(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, spec(n, 0), F, 2, 0, 1, p->s2_nl, s),
-                    "x pass fwd");
+        std::vector<float2*> spec_delta(n_max + 1, nullptr);
+        for (int n = 2; n <= n_max; ++n) spec_delta[n] = spec(n, 0);
+        const double fb = 4.0 * (double)field_floats(p);
+        // Orders m = 1..n_max. Below start_order the spectra are given; from there
+        // on delta_m, theta_m arrive as real fields from the pair products of
+        // the lower orders and are transformed forward first.
+        for (int m = 1; m <= n_max; ++m) {
+            const bool given = m == 1 || m < start_order;
+            float2* dk = m == 1 ? d1 : spec(m, 0);
+            float2* tk = m == 1 ? d1 : spec(m, 1);
+            if (!given) {
+                CKP(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, dk, dk, F, 2, 1.0f, s), "z r2c");
+                CKP(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 1, 0, -1, s), "y pass fwd");
+                if (m == n_max) {
+                    CKP(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 1, p->s2_nl, s), "x pass fwd");
+                    break;
+                }
+            }
+            if (m == n_max) break;
+            if (gridspt_status st = derive_order(p, m, dk, tk, w, !given, start_order, spec_delta, s)) return st;
+            if (2 * m <= n_max && 2 * m >= start_order) {   // diagonal pair (m, m) of order 2m
+                ProductArgs pa{};
+                pa.ws = w;
+                pa.cells = field_floats(p);
+                for (int q = 1; q <= kMaxOrder; ++q) pa.base[q] = order_base(q);
+                pa.n = 2 * m;
+                pa.diag_only = m;
+                if (2 * m == 2) {   // order 2 has no other pair: write delta_2, theta_2
+                    pa.out_delta = reinterpret_cast<float*>(spec(2, 0));
+                    pa.out_theta = reinterpret_cast<float*>(spec(2, 1));
+                    recursion_coefs(p, 2, &pa.cdA, &pa.cdB, &pa.ctA, &pa.ctB);
+                } else {            // first (partial) contribution to order 2m
+                    float* acc = w + (long long)(acc_base(n_max) + 2 * (2 * m - 4)) * field_floats(p);
+                    pa.out_delta = acc;
+                    pa.out_theta = acc + field_floats(p);
+                    pa.cdA = 1.f;
+                    pa.cdB = 0.f;
+                    pa.ctA = 0.f;
+                    pa.ctB = 1.f;
+                }
+                CKP(PK_PRODUCT, fb * (m == 1 ? 13 + 2 : 17 + 2), s, launch_product(p->geo, pa, s), "diagonal pair");
             }
         }
     }
@@ -645,7 +773,7 @@ gridspt_status gridspt_batch_destroy(gridspt_batch b) {
 // ------------------------------------------------------------- autotuner
 gridspt_status gridspt_autotune_scratch_size(gridspt_plan p, size_t* bytes) {
     if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
-    *bytes = 4 * (size_t)field_floats(p) * sizeof(float);
+    *bytes = 29 * (size_t)field_floats(p) * sizeof(float);   // 2 spectra + 7 + 12 + 17 expansion fields (overlapping)
     return GRIDSPT_OK;
 }
 
@@ -685,35 +813,34 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
         cudaEventDestroy(a);
         return cuda_fail(e, "event");
     }
-    // one representative launch per pass on fields 0..3
+    // per pass, the launch of an order >= 2 expansion (x: 2 spectra -> 7, y: 7 -> 12,
+    // z: 12 -> 17) or of the forward passes of delta_n, theta_n, on scratch fields
     auto run = [&](const Geo& g, int pass) -> cudaError_t {
+        XExpArgs xa{};
+        YZExpArgs ya{}, za{};
+        expansion_codes(2, xa, ya, za);
         switch (pass) {
             case TV_COLPASS: return launch_colpass_fwd(g, f0, F, 2, 1, 0, -1, s);
-            case TV_XEXP: {
-                XExpArgs xa{};
+            case TV_XEXP:
                 xa.src0 = f0;
                 xa.src1 = f0 + F;
                 xa.out = f0 + 2 * F;
                 xa.out_stride = F;
-                xa.nout = 2;
-                xa.codes[0] = x_code(XK_POW, 0, XS_DELTA);
-                xa.codes[1] = x_code(XK_POW, 1, XS_PHI);
                 xa.s2_nl = -1;
                 return launch_xexp(g, xa, s);
-            }
             case TV_YEXP:
-            case TV_ZEXP: {
-                YZExpArgs ya{};
-                ya.in = f0 + 2 * F;
+                ya.in = f0;
                 ya.in_stride = F;
-                ya.out = f0;
+                ya.out = f0 + 7 * F;
                 ya.out_stride = F;
-                ya.nout = 2;
-                ya.codes[0] = pass == TV_YEXP ? y_code(0, 0, 0) : z_code(0, 0, 0, 0);
-                ya.codes[1] = pass == TV_YEXP ? y_code(1, 1, 1) : z_code(1, 1, 1, 1);
-                return pass == TV_YEXP ? launch_yexp(g, ya, s) : launch_zexp(g, ya, s);
-            }
-            default: return launch_zr2c(g, f0 + 2 * F, f0 + 2 * F, F, 2, 1.0f, s);
+                return launch_yexp(g, ya, s);
+            case TV_ZEXP:
+                za.in = f0;
+                za.in_stride = F;
+                za.out = f0 + 12 * F;
+                za.out_stride = F;
+                return launch_zexp(g, za, s);
+            default: return launch_zr2c(g, f0, f0, F, 2, 1.0f, s);
         }
     };
     int best[TV_COUNT];

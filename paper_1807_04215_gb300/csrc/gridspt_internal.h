@@ -84,6 +84,33 @@ struct IcArgs {
     long long s2_cut;      // keep 0 < |s|^2 <= s2_cut
 };
 
+// z expansion fused with accumulate-ahead pair products (Eq. recursion_formula):
+// while the real derived fields of order m are formed one by one, each is
+// multiplied with its partner fields of stored lower orders j and summed into
+// A_{m+j}, B_{m+j}. Target t ends either in accumulator fields (partial) or,
+// for its last pair, in delta_n, theta_n.
+constexpr int kMaxPairTargets = 2;
+struct PairTarget {
+    const float* partner;       // stored real fields of order j: field f at partner + f * cells
+    const float* acc_in_a;      // partial A, B from earlier pairs (NULL: none)
+    const float* acc_in_b;
+    float* out_a;               // out_a = ca0 A + ca1 B, out_b = cb0 A + cb1 B
+    float* out_b;
+    float ca0, ca1, cb0, cb1;
+    int pcount[17];             // per produced slot: number of partner fields (0..2)
+    int pfield[17][2];          // partner field index in the stored order
+    float pcoef_a[17][2];       // contribution coefficients to A and B
+    float pcoef_b[17][2];
+};
+struct ZPairArgs {
+    YZExpArgs z;                // inputs (xy-fields) and output list (slot = derived-field slot)
+    float* store;               // real fields of this order (slot s at store + s * cells) or NULL
+    long long cells;            // N^3
+    int ntargets;
+    PairTarget t[kMaxPairTargets];
+};
+cudaError_t launch_zexp_pairs(const Geo& g, const ZPairArgs& a, cudaStream_t s);
+
 struct ProductArgs {
     const float* ws;       // derived fields; order m field j at ws + (base[m] + j) * cells
     long long cells;       // N^3
@@ -92,6 +119,7 @@ struct ProductArgs {
     float* out_delta;      // real field written (4 N^3 bytes)
     float* out_theta;
     float cdA, cdB, ctA, ctB;  // recursion coefficients times N^-3
+    int diag_only;             // > 0: only the pair (diag_only, diag_only)
 };
 
 struct BinSpec {

@@ -18,6 +18,8 @@
 //
 // Four adjacent cells per thread (16-byte loads and stores). The output is
 // scaled by N^-3 so that the following forward transform is unnormalised.
+// With diag_only = m only the pair (m, m) of order n = 2m is formed (used by the
+// accumulate-ahead schedule, where the other pairs are summed in the z pass).
 #include "gridspt_internal.h"
 
 namespace gridspt {
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256) k_product(ProductArgs a) {
     const float4* ws = reinterpret_cast<const float4*>(a.ws);
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
     const int n = a.n;
-    for (int m = 1; 2 * m <= n; ++m) {
+    for (int m = a.diag_only > 0 ? a.diag_only : 1; 2 * m <= n; ++m) {
         const int mh = n - m;   // held (higher) order
         Held H;
         load_order(H, ws + (long long)a.base[mh] * n4 + i, n4, mh);
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(256) k_product(ProductArgs a) {
             diagonal(H, A, B);
         else
             stream_order(ws + (long long)a.base[m] * n4 + i, n4, m, H, A, B);
+        if (a.diag_only > 0) break;
     }
     float4 d, t;
     d.x = fmaf(a.cdA, A.x, a.cdB * B.x);

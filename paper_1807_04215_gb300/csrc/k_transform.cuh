@@ -425,6 +425,141 @@ k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
     if constexpr (PREFETCH) cp_async_wait_all();
 }
 
+// ------------------------------- z expansion fused with pair products
+// Forms the real derived fields of one order m like k_zexp and, while each
+// field f is in registers, multiplies it with its partner fields g of stored
+// lower orders j (loaded tile by tile) and accumulates the pair terms of
+// Eq. recursion_formula into A_{m+j}, B_{m+j} held in registers:
+//   A += coef_a f g, B += coef_b f g   (coefficients per (f, g), both ordered
+//   pairs (m, j) and (j, m) included; see PairTarget). After the last field the
+// partial sums from earlier pairs are added and the targets are written as
+// accumulator fields or, for a target's last pair, as delta_n, theta_n
+// (recursion coefficients and N^-3 folded into ca0.., cb1). The fields of
+// order m are stored only when a later order still needs them.
+template <int N, int TZ, int NT>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PZ, 1)
+k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
+    constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NTH = TZ * P;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tin = sm + N;                      // input xy-field tile
+    float2* tex = tin + TZ * PITCH;            // output tile / exchange buffer
+    float2* tpt = tex + TZ * PITCH;            // partner tile
+    const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
+    load_table(tw, twg, N);
+    const long long rows = (long long)N * N;
+    const long long row0 = (long long)blockIdx.x * TZ;
+    const YZExpArgs& z = args.z;
+    // real fields as rows of M float2 (cells 2k, 2k + 1)
+    const long long fstride2 = args.cells / 2;
+    float2 accA[NT][E], accB[NT][E];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int i = 0; i < E; ++i) accA[t][i] = accB[t][i] = make_float2(0.f, 0.f);
+    int cur = -1;
+    for (int f = 0; f < z.nout; ++f) {
+        const int code = z.codes[f];
+        const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
+        if (in != cur) {
+            __syncthreads();
+            tile_load<M, TZ, PITCH, NTH>(tin, z.in + in * z.in_stride, row0, rows);
+            __syncthreads();
+            cur = in;
+        }
+        const float2* colp = tin + c * PITCH;
+        float2 x[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = p + P * i;
+            float2 Xk = colp[k];
+            float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
+            if (g) {
+                const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
+                Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);
+                Xm = cscale(Xm, g == 1 ? k2 : k2 * k2);
+            }
+            if (cc == 1) {
+                Xk = cmul_i<+1>(Xk);
+                Xm = cmul_i<+1>(Xm);
+            } else if (cc == 2) {
+                Xk = cmul_i<-1>(Xk);
+                Xm = cmul_i<-1>(Xm);
+            }
+            Xm = cconj(Xm);
+            const float2 Ev = cadd(Xk, Xm);
+            const float2 Ov = cmul(csub(Xk, Xm), tw[k]);
+            x[i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
+        }
+        __syncthreads();
+        float2* colx = tex + c * PITCH;
+        fft_column<M, +1, N>(x, p, colx, 1, tw);   // x[i]: real cells 2n, 2n + 1 of row c, n = p + P i
+        if (args.store) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) colx[p + P * i] = x[i];
+            __syncthreads();
+            tile_store<M, TZ, PITCH, NTH>(reinterpret_cast<float2*>(args.store) + slot * fstride2, tex, row0, rows);
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            if (t >= args.ntargets) break;
+            const PairTarget& T = args.t[t];
+            for (int q = 0; q < T.pcount[slot]; ++q) {
+                __syncthreads();
+                tile_load<M, TZ, PITCH, NTH>(tpt, reinterpret_cast<const float2*>(T.partner) +
+                                                      (long long)T.pfield[slot][q] * fstride2, row0, rows);
+                __syncthreads();
+                const float ca = T.pcoef_a[slot][q], cb = T.pcoef_b[slot][q];
+                const float2* pr = tpt + c * PITCH;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const float2 gv = pr[p + P * i];
+                    const float2 fg = make_float2(x[i].x * gv.x, x[i].y * gv.y);
+                    accA[t][i].x = fmaf(ca, fg.x, accA[t][i].x);
+                    accA[t][i].y = fmaf(ca, fg.y, accA[t][i].y);
+                    accB[t][i].x = fmaf(cb, fg.x, accB[t][i].x);
+                    accB[t][i].y = fmaf(cb, fg.y, accB[t][i].y);
+                }
+            }
+        }
+    }
+    // targets: add earlier partial sums, combine, write (via the output tile)
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        if (t >= args.ntargets) break;
+        const PairTarget& T = args.t[t];
+        if (T.acc_in_a) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __syncthreads();
+                tile_load<M, TZ, PITCH, NTH>(tpt, reinterpret_cast<const float2*>(h ? T.acc_in_b : T.acc_in_a),
+                                             row0, rows);
+                __syncthreads();
+                const float2* pr = tpt + c * PITCH;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const float2 v = pr[p + P * i];
+                    float2& a = h ? accB[t][i] : accA[t][i];
+                    a.x += v.x;
+                    a.y += v.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float c0 = h ? T.cb0 : T.ca0, c1 = h ? T.cb1 : T.ca1;
+            __syncthreads();
+            float2* colx = tex + c * PITCH;
+#pragma unroll
+            for (int i = 0; i < E; ++i)
+                colx[p + P * i] = make_float2(fmaf(c0, accA[t][i].x, c1 * accB[t][i].x),
+                                              fmaf(c0, accA[t][i].y, c1 * accB[t][i].y));
+            __syncthreads();
+            tile_store<M, TZ, PITCH, NTH>(reinterpret_cast<float2*>(h ? T.out_b : T.out_a), tex, row0, rows);
+        }
+    }
+}
+
 // ------------------------------------------------- TMA-staged y expansion
 // Same computation as k_yexp, but each input column tile (all N rows of TZ
 // adjacent kz columns of one x plane) is copied into shared memory by the
@@ -746,6 +881,20 @@ struct Launch {
         k_yexp_tma<N, TZ><<<grid, TZ * PC, smem, s>>>(a, map, g.tw, (float)g.kF, g.status);
         return cudaGetLastError();
     }
+    static cudaError_t zexp_pairs(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
+        const long long rows = (long long)N * N;
+        dim3 grid((unsigned)((rows + TZZ - 1) / TZZ));
+        const size_t smem = sizeof(float2) * (N + 3 * (size_t)TZZ * PITCH);
+        cudaError_t e;
+        if (a.ntargets <= 1) {
+            if ((e = set_smem(k_zexp_pairs<N, TZZ, 1>, smem)) != cudaSuccess) return e;
+            k_zexp_pairs<N, TZZ, 1><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+        } else {
+            if ((e = set_smem(k_zexp_pairs<N, TZZ, 2>, smem)) != cudaSuccess) return e;
+            k_zexp_pairs<N, TZZ, 2><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+        }
+        return cudaGetLastError();
+    }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
     static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, double* partial,
                               cudaStream_t s) {
@@ -789,6 +938,9 @@ struct Launch {
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<false>(g, a, s);                   \
     }                                                                                                      \
     int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
+    cudaError_t transform_zexp_pairs_##N(const Geo& g, const ZPairArgs& a, cudaStream_t s) {               \
+        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zexp_pairs(g, a, s);                                 \
+    }                                                                                                      \
     cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band, int nf,       \
                                      double* partial, cudaStream_t s) {                                    \
         return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zshell(g, in, st, band, nf, partial, s);             \

@@ -16,6 +16,7 @@ namespace gridspt {
     cudaError_t transform_yexp_##N(const Geo&, const YZExpArgs&, int, cudaStream_t);                       \
     cudaError_t transform_zexp_##N(const Geo&, const YZExpArgs&, int, cudaStream_t);                       \
     int transform_shell_blocks_##N();                                                                      \
+    cudaError_t transform_zexp_pairs_##N(const Geo&, const ZPairArgs&, cudaStream_t);                      \
     cudaError_t transform_zshell_##N(const Geo&, const float2*, long long, int, int, double*, cudaStream_t);
 GRIDSPT_ALL_N(GRIDSPT_DECLARE)
 #undef GRIDSPT_DECLARE
@@ -72,6 +73,15 @@ cudaError_t launch_yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
 cudaError_t launch_zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
     switch (g.N) {
 #define GRIDSPT_CASE(n) case n: return transform_zexp_##n(g, a, g.var[TV_ZEXP], s);
+        GRIDSPT_ALL_N(GRIDSPT_CASE)
+#undef GRIDSPT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_zexp_pairs(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
+    switch (g.N) {
+#define GRIDSPT_CASE(n) case n: return transform_zexp_pairs_##n(g, a, s);
         GRIDSPT_ALL_N(GRIDSPT_CASE)
 #undef GRIDSPT_CASE
         default: return cudaErrorInvalidValue;
