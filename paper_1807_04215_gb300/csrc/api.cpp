@@ -497,6 +497,12 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
             bytes += fb * (j == 1 ? 13 : 17) + fb * 2 + (T.acc_in_a ? fb * 2 : 0);
         }
         if (!a.store && a.ntargets == 0) break;
+        if (a.ntargets == 0) {   // store only: the plain z expansion
+            YZExpArgs zs = za;
+            zs.out = reinterpret_cast<float2*>(a.store);
+            CKP(PK_ZEXP, bytes, s, launch_zexp(p->geo, zs, s), "z expansion");
+            break;
+        }
         CKP(PK_ZEXP, bytes, s, launch_zexp_pairs(p->geo, a, s), "z expansion and pair products");
     } while (first < js.size());
     return GRIDSPT_OK;

@@ -440,11 +440,12 @@ template <int N, int TZ, int NT>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, 1)
 k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NTH = TZ * P;
+    constexpr int MAXP = 3;                    // partner fields of one output over all targets
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tin = sm + N;                      // input xy-field tile
     float2* tex = tin + TZ * PITCH;            // output tile / exchange buffer
-    float2* tpt = tex + TZ * PITCH;            // partner tile
+    float2* tpt = tex + TZ * PITCH;            // MAXP partner tiles
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
     const long long rows = (long long)N * N;
@@ -461,8 +462,19 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     for (int f = 0; f < z.nout; ++f) {
         const int code = z.codes[f];
         const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
+        __syncthreads();                       // tiles of the previous output no longer read
+        // partner tiles of this output: copies issued now, consumed after the transform
+        int np = 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            if (t >= args.ntargets) break;
+            const PairTarget& T = args.t[t];
+            for (int q = 0; q < T.pcount[slot]; ++q, ++np)
+                tile_prefetch<M, TZ, PITCH, NTH>(tpt + np * TZ * PITCH, reinterpret_cast<const float2*>(T.partner) +
+                                                                         (long long)T.pfield[slot][q] * fstride2,
+                                                 row0, rows);
+        }
         if (in != cur) {
-            __syncthreads();
             tile_load<M, TZ, PITCH, NTH>(tin, z.in + in * z.in_stride, row0, rows);
             __syncthreads();
             cur = in;
@@ -491,26 +503,24 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
             const float2 Ov = cmul(csub(Xk, Xm), tw[k]);
             x[i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
         }
-        __syncthreads();
         float2* colx = tex + c * PITCH;
         fft_column<M, +1, N>(x, p, colx, 1, tw);   // x[i]: real cells 2n, 2n + 1 of row c, n = p + P i
+        cp_async_wait_all();
         if (args.store) {
 #pragma unroll
             for (int i = 0; i < E; ++i) colx[p + P * i] = x[i];
-            __syncthreads();
-            tile_store<M, TZ, PITCH, NTH>(reinterpret_cast<float2*>(args.store) + slot * fstride2, tex, row0, rows);
         }
+        __syncthreads();                           // partner tiles and the output tile are complete
+        if (args.store)
+            tile_store<M, TZ, PITCH, NTH>(reinterpret_cast<float2*>(args.store) + slot * fstride2, tex, row0, rows);
+        np = 0;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             if (t >= args.ntargets) break;
             const PairTarget& T = args.t[t];
-            for (int q = 0; q < T.pcount[slot]; ++q) {
-                __syncthreads();
-                tile_load<M, TZ, PITCH, NTH>(tpt, reinterpret_cast<const float2*>(T.partner) +
-                                                      (long long)T.pfield[slot][q] * fstride2, row0, rows);
-                __syncthreads();
+            for (int q = 0; q < T.pcount[slot]; ++q, ++np) {
                 const float ca = T.pcoef_a[slot][q], cb = T.pcoef_b[slot][q];
-                const float2* pr = tpt + c * PITCH;
+                const float2* pr = tpt + np * TZ * PITCH + c * PITCH;
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     const float2 gv = pr[p + P * i];
@@ -884,7 +894,7 @@ struct Launch {
     static cudaError_t zexp_pairs(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
         const long long rows = (long long)N * N;
         dim3 grid((unsigned)((rows + TZZ - 1) / TZZ));
-        const size_t smem = sizeof(float2) * (N + 3 * (size_t)TZZ * PITCH);
+        const size_t smem = sizeof(float2) * (N + 5 * (size_t)TZZ * PITCH);   // input, output, 3 partner tiles
         cudaError_t e;
         if (a.ntargets <= 1) {
             if ((e = set_smem(k_zexp_pairs<N, TZZ, 1>, smem)) != cudaSuccess) return e;
