@@ -33,7 +33,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic / algorithmic bytes measured by ncu for the kernels as they stand
 # (profiles/k_xexp_k_yexp_k_zexp_c2r-512.md: 512^3, one field per launch);
 # traffic per launch is reported as this ratio times the launch's algorithmic bytes
-NCU_TRAFFIC_RATIO = {"z_expand": 0.969, "y_expand": 0.969, "x_expand": 0.966}
+NCU_TRAFFIC_RATIO = {"y_expand": 0.969, "x_expand": 0.966}
 
 
 def log_edges(lo, hi, nb):
