@@ -48,6 +48,12 @@ struct Cfg {
     static constexpr int TZZ0 = cmin(cmin(64, cmax(16, 256 / PZ)), 1024 / PZ);
     static constexpr int TZZ1 = N >= 128 ? (2 * TZZ0 * PZ <= 1024 ? 2 * TZZ0 : cmax(16, TZZ0 / 2)) : TZZ0;
     static constexpr int PITCH = M + 1;
+    // fused z pass with pair products: five tiles (input, exchange, 3 partners)
+    // must fit the 227 KB a block may hold; halve the row count until they do
+    static constexpr size_t pair_smem(int tz) { return sizeof(float2) * (N + 5 * (size_t)tz * PITCH); }
+    static constexpr int TZP = pair_smem(TZZ0) <= 232448 ? TZZ0
+                             : pair_smem(TZZ0 / 2) <= 232448 ? TZZ0 / 2 : TZZ0 / 4;
+    static_assert(pair_smem(TZP) <= 232448, "fused z pass tiles exceed shared memory");
 };
 
 __device__ __forceinline__ int signed_idx(int n, int N) { return n < N / 2 ? n : n - N; }
@@ -949,7 +955,7 @@ struct Launch {
     }                                                                                                      \
     int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
     cudaError_t transform_zexp_pairs_##N(const Geo& g, const ZPairArgs& a, cudaStream_t s) {               \
-        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zexp_pairs(g, a, s);                                 \
+        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZP>::zexp_pairs(g, a, s);                                 \
     }                                                                                                      \
     cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band, int nf,       \
                                      double* partial, cudaStream_t s) {                                    \

@@ -87,18 +87,27 @@ def test_1024_properties():
     ms = e0.elapsed_time(e1)
     rep = {"ms": round(ms, 1), "Mcells_orders_per_s": round(N ** 3 * n_max / ms / 1e3, 1), "mass": {}}
     for n in range(2, n_max + 1):
+        # delta_n(0) = 0 in exact arithmetic (mass conservation). In FP32 it is
+        # the mean of real-space products whose means cancel, so its rounding
+        # error scales with the cell RMS of delta_n, sqrt(sum_k |delta_n(k)|^2)
+        # (Parseval; the half spectrum counts kz > 0 modes twice). Bound: 16 u.
         z = abs(complex(sp[0, n - 2, 0, 0, 0, 0].item()))
-        rms = float(torch.sqrt(torch.mean(torch.abs(sp[0, n - 2, 0]) ** 2)).item())
-        rep["mass"][n] = float(f"{z / rms:.2e}")
-        assert z <= 1e-4 * rms          # delta_n(0) = 0 in exact arithmetic (mass conservation, in band)
+        a2 = torch.abs(sp[0, n - 2, 0]) ** 2
+        rms_cell = math.sqrt(2 * float(a2.sum(dtype=torch.float64)) - float(a2[:, :, 0].sum(dtype=torch.float64)))
+        del a2
+        rep["mass"][n] = float(f"{z / rms_cell:.2e}")
+        assert z <= 16 * 2.0 ** -24 * rms_cell
     # exact 2^n scaling (every step is linear or a product; scaling by 2 is exact)
+    # (a second spectra buffer does not fit beside the workspace: a slab of 16 kx
+    # planes of every order is kept and compared bitwise)
+    slab = sp[0, :, :, :16].clone()
     d2 = d1 * 2
-    sp2 = torch.empty_like(sp)
-    g.run_orders(plan, d2, spectra=sp2, ws=ws)
+    g.run_orders(plan, d2, spectra=sp, ws=ws)
     del d2
     for n in range(2, n_max + 1):
-        assert torch.equal(sp2[0, n - 2], sp[0, n - 2] * (2.0 ** n))
-    del sp2
+        assert torch.equal(sp[0, n - 2, :, :16], slab[n - 2] * (2.0 ** n))
+    del slab, ws, sp
+    torch.cuda.empty_cache()
     kF = 2 * math.pi / L
     edges = [kF * (b + 0.5) for b in range(4, 60, 4)]
     p, nk = g.power(plan, d1[0], d1[0], edges)
