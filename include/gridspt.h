@@ -206,15 +206,18 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
 /* Autotuner for the transform passes (not part of the paper's method). Each
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
  * 4 contiguous-axis forward pass) has two variants for N >= 128 (identical for
- * smaller N); the y expansion has a third, TMA-staged one (N >= 128). gridspt_autotune times both variants of every
- * pass on `scratch` (device, >= gridspt_autotune_scratch_size bytes, contents
- * overwritten) with CUDA events on `stream`, keeps the faster one in the plan
- * and writes the choices to choices_out (host int32[5], may be NULL). It
- * synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning store and
- * read the choices (0 or 1; 0..2 for the y expansion), e.g. from a cache kept
- * by the caller.
- * Results are bitwise identical for both variants: they only change how
- * columns and rows are grouped into thread blocks. */
+ * smaller N). The y expansion has a third, TMA-staged one (N >= 128). The z
+ * expansion (with the fused pair products of the recursion) has a third that
+ * runs one z row per warp without block-wide barriers (power-of-two N <= 512;
+ * other sizes run variant 0 when it is chosen). gridspt_autotune times the
+ * variants of every pass on `scratch` (device, >= gridspt_autotune_scratch_size
+ * bytes, contents overwritten) with CUDA events on `stream`, keeps the fastest
+ * in the plan and writes the choices to choices_out (host int32[5], may be
+ * NULL). It synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning
+ * store and read the choices (0 or 1; 0..2 for the y and z expansions), e.g.
+ * from a cache kept by the caller.
+ * Results are bitwise identical for all variants: they only change how
+ * columns and rows are grouped into thread blocks and warps. */
 gridspt_status gridspt_autotune_scratch_size(gridspt_plan plan, size_t* bytes);
 gridspt_status gridspt_autotune(gridspt_plan plan, void* scratch, size_t scratch_bytes, int32_t* choices_out,
                                 gridspt_stream stream);

@@ -469,8 +469,14 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
         a.store = (store && first == 0) ? ws + (long long)order_base(m) * cells : nullptr;
         a.ntargets = 0;
         double bytes = fb * za.nout * (a.store ? 1 : 0) + fb * (m == 1 ? 9 : 12);   // stores + xy-field inputs
+        // a launch holds at most kMaxPairTargets targets and kMaxPartners partner
+        // fields per output over all its targets (order 1 supplies at most one
+        // partner per output, higher orders two)
+        int partners = 0;
         for (size_t q = first; q < js.size() && a.ntargets < kMaxPairTargets; ++q, ++first) {
             const int j = js[q], n = m + j;
+            if (partners + (j == 1 ? 1 : 2) > kMaxPartners) break;
+            partners += j == 1 ? 1 : 2;
             PairTarget& T = a.t[a.ntargets++];
             T.partner = ws + (long long)order_base(j) * cells;
             pair_table(j, T);
@@ -495,6 +501,11 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
                 T.cb1 = 1.f;
             }
             bytes += fb * (j == 1 ? 13 : 17) + fb * 2 + (T.acc_in_a ? fb * 2 : 0);
+        }
+        for (int sl = 0; sl < 17; ++sl) {   // the kernels stage at most kMaxPartners partner tiles
+            int c = 0;
+            for (int t = 0; t < a.ntargets; ++t) c += a.t[t].pcount[sl];
+            if (c > kMaxPartners) return fail(GRIDSPT_E_INVALID, "internal: %d partner fields for one output", c);
         }
         if (!a.store && a.ntargets == 0) break;
         if (a.ntargets == 0) {   // store only: the plain z expansion
@@ -840,12 +851,31 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
                 ya.out = f0 + 7 * F;
                 ya.out_stride = F;
                 return launch_yexp(g, ya, s);
-            case TV_ZEXP:
+            case TV_ZEXP: {
                 za.in = f0;
                 za.in_stride = F;
                 za.out = f0 + 12 * F;
                 za.out_stride = F;
-                return launch_zexp(g, za, s);
+                cudaError_t ez = launch_zexp(g, za, s);
+                if (ez != cudaSuccess) return ez;
+                // and the form fused with pair products: one target, order-1
+                // partners in fields 0..12, partial sums in from fields 13, 14,
+                // outputs to fields 15, 16 (nothing written is read in the launch)
+                ZPairArgs pa{};
+                pa.z = za;
+                pa.cells = field_floats(p);
+                pa.ntargets = 1;
+                PairTarget& T = pa.t[0];
+                T.partner = reinterpret_cast<const float*>(f0);
+                pair_table(1, T);
+                T.acc_in_a = reinterpret_cast<const float*>(f0 + 13 * F);
+                T.acc_in_b = reinterpret_cast<const float*>(f0 + 14 * F);
+                T.out_a = reinterpret_cast<float*>(f0 + 15 * F);
+                T.out_b = reinterpret_cast<float*>(f0 + 16 * F);
+                T.ca0 = T.cb1 = 1.f;
+                T.ca1 = T.cb0 = 0.f;
+                return launch_zexp_pairs(g, pa, s);
+            }
             default: return launch_zr2c(g, f0, f0, F, 2, 1.0f, s);
         }
     };

@@ -171,4 +171,112 @@ __device__ __forceinline__ void fft_column(float2 (&x)[fft_elems(L)], int p, flo
     fft_stages<L, 0, DIR, N>(x, p, col, SN, tw);
 }
 
+
+// ------------------------------------------------------- warp-row variant
+// The same transform with the P threads of one length-L row on P consecutive
+// lanes of one warp (P <= 32 and 32 % P == 0, so a warp holds 32 / P rows):
+// the stage exchanges go through a per-warp buffer, ordered by __syncwarp, so
+// rows never wait on a block-wide barrier. Stage arithmetic and twiddle values
+// are those of fft_stage, so results are bitwise equal.
+//
+// Exchange buffer: element n of a row at xpad(n) = n + n / 16 (one float2 of
+// padding per 16). With it every stage's scatter writes and gather reads of a
+// warp take the minimum two shared-memory wavefronts for power-of-two L.
+//
+// Stage twiddles are read from a lane-major table twl[j][p] (conflict-free,
+// identical for every row): j enumerates (stage S >= 1, butterfly q, t >= 1).
+__device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
+
+template <int L>
+__host__ __device__ constexpr int fft_row_tw_count(int S) {   // stage twiddles of stages < S
+    return S <= 0 ? 0
+                  : fft_row_tw_count<L>(S - 1) +
+                        (fft_ls(L, S - 1) > 1 ? (fft_elems(L) / fft_radix(L, S - 1)) * (fft_radix(L, S - 1) - 1) : 0);
+}
+template <int L>
+__host__ __device__ constexpr int fft_row_tw_total() { return fft_row_tw_count<L>(fft_nstages(L)); }
+
+// Fill twl[j * P + p] for p < P from the shared table of N-th roots tw.
+template <int L, int N, int S = 0>
+__device__ __forceinline__ void fft_row_twiddles(float2* twl, const float2* tw, int p) {
+    if constexpr (S < fft_nstages(L)) {
+        constexpr int E = fft_elems(L), P = L / E, R = fft_radix(L, S), Ls = fft_ls(L, S), Q = E / R;
+        constexpr int TWS = N / (Ls * R);
+        if constexpr (Ls > 1) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int k = (p + q * P) % Ls;
+#pragma unroll
+                for (int t = 1; t < R; ++t)
+                    twl[(fft_row_tw_count<L>(S) + q * (R - 1) + (t - 1)) * P + p] = tw[t * k * TWS];
+            }
+        }
+        fft_row_twiddles<L, N, S + 1>(twl, tw, p);
+    }
+}
+
+template <int L, int S, int DIR>
+__device__ __forceinline__ void fft_row_stage(float2 (&x)[fft_elems(L)], int p, float2* row,
+                                              const float2* __restrict__ twl) {
+    constexpr int E = fft_elems(L);
+    constexpr int P = L / E;
+    constexpr int R = fft_radix(L, S);
+    constexpr int Ls = fft_ls(L, S);
+    constexpr int Q = E / R;
+    constexpr bool last = (S == fft_nstages(L) - 1);
+    constexpr int J0 = fft_row_tw_count<L>(S);
+    float2 y[E];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 v[R];
+        const int b = p + q * P;
+        const int k = (Ls == 1) ? 0 : (b % Ls);
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = x[q + t * Q];
+        if constexpr (Ls > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w = twl[(J0 + q * (R - 1) + (t - 1)) * P + p];
+                if (DIR < 0) w.y = -w.y;
+                v[t] = cmul(v[t], w);
+            }
+        }
+        dft_small<R, DIR>(v);
+        if constexpr (last) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) y[q + t * Q] = v[t];
+        } else {
+            const int base = (b / Ls) * Ls * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) row[xpad(base + t * Ls)] = v[t];
+        }
+    }
+    if constexpr (last) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = y[i];
+    } else {
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = row[xpad(p + P * i)];
+        __syncwarp();
+    }
+}
+
+template <int L, int S, int DIR>
+__device__ __forceinline__ void fft_row_stages(float2 (&x)[fft_elems(L)], int p, float2* row,
+                                               const float2* __restrict__ twl) {
+    if constexpr (S < fft_nstages(L)) {
+        fft_row_stage<L, S, DIR>(x, p, row, twl);
+        fft_row_stages<L, S + 1, DIR>(x, p, row, twl);
+    }
+}
+
+// Full length-L transform of one row held by P lanes (exchange buffer `row`,
+// padded layout). Every lane of the warp must call it the same number of times.
+template <int L, int DIR>
+__device__ __forceinline__ void fft_row(float2 (&x)[fft_elems(L)], int p, float2* row,
+                                        const float2* __restrict__ twl) {
+    fft_row_stages<L, 0, DIR>(x, p, row, twl);
+}
+
 }  // namespace gridspt

@@ -25,7 +25,7 @@ struct Geo {
 };
 
 // number of tile variants per pass (the autotuner times each)
-constexpr int kTuneVariants[TV_COUNT] = {2, 2, 3, 2, 2};
+constexpr int kTuneVariants[TV_COUNT] = {2, 2, 3, 3, 2};
 
 // Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every
 // derived field is c * kx^a * ky^b * kz^g * src(k) with src in {delta, theta,
@@ -90,6 +90,7 @@ struct IcArgs {
 // A_{m+j}, B_{m+j}. Target t ends either in accumulator fields (partial) or,
 // for its last pair, in delta_n, theta_n.
 constexpr int kMaxPairTargets = 2;
+constexpr int kMaxPartners = 3;      // partner fields of one output over a launch's targets
 struct PairTarget {
     const float* partner;       // stored real fields of order j: field f at partner + f * cells
     const float* acc_in_a;      // partial A, B from earlier pairs (NULL: none)

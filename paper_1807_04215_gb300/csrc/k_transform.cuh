@@ -446,7 +446,7 @@ template <int N, int TZ, int NT>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, 1)
 k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NTH = TZ * P;
-    constexpr int MAXP = 3;                    // partner fields of one output over all targets
+    constexpr int MAXP = kMaxPartners;         // partner fields of one output over all targets
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tin = sm + N;                      // input xy-field tile
@@ -572,6 +572,203 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                                               fmaf(c0, accA[t][i].y, c1 * accB[t][i].y));
             __syncthreads();
             tile_store<M, TZ, PITCH, NTH>(reinterpret_cast<float2*>(h ? T.out_b : T.out_a), tex, row0, rows);
+        }
+    }
+}
+
+// ------------------------------------- z pass on warp rows (no block barriers)
+// The computation of k_zexp (NT = 0, store only) and k_zexp_pairs (NT = 1, 2
+// targets) with one z row per P consecutive lanes of a warp (P = M / E <= 32,
+// 32 / P rows per warp) instead of block-wide tiles. Each warp runs its rows
+// through every output field on its own:
+//   * the xy-field input rows (contiguous, 16-byte vector loads) are kept in a
+//     per-warp buffer while consecutive outputs share them;
+//   * the partner rows of the output are copied into per-warp buffers by
+//     16-byte cp.async before the transform and consumed after it;
+//   * the transform exchanges through a per-warp padded buffer (fft_row);
+//   * stores, accumulator inputs and the targets' outputs go straight between
+//     registers and global memory: lane p holds elements p + P i, so every
+//     warp access covers whole rows.
+// The only block barrier follows the twiddle table set-up. Persistent grid:
+// each warp strides over the row groups. Results are bitwise those of the
+// tile kernels (same transform arithmetic, same accumulation order).
+constexpr int kRowWarps = 8;
+
+template <int N>
+struct RowCfg {
+    static constexpr int M = N / 2, E = fft_elems(M), P = M / E;
+    static constexpr bool ok = (M & (M - 1)) == 0 && P <= 32 && 32 % P == 0;
+    static constexpr int RW = ok ? 32 / P : 1;               // rows per warp
+    static constexpr int XROW = M + (M >> 4);                 // padded exchange row
+    static constexpr int NTW = fft_row_tw_total<M>();
+    static constexpr int HDR = ((NTW + E) * P + 1) / 2 * 2;   // twiddle tables, 16-byte multiple
+    static constexpr int MAXP = kMaxPartners;
+    static constexpr int WIN = RW * M;                        // input rows of a warp
+    static constexpr int WSTRIDE = WIN * (1 + MAXP) + RW * XROW;
+    static constexpr size_t smem(int nt) {
+        return sizeof(float2) * (HDR + (size_t)kRowWarps * (nt ? WSTRIDE : WIN + RW * XROW));
+    }
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+template <int N, int NT>
+__global__ void __launch_bounds__(kRowWarps * 32, 2)
+k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
+    using C = RowCfg<N>;
+    constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW, WIN = C::WIN;
+    constexpr int NA = NT > 0 ? NT : 1;
+    static_assert(C::ok, "warp-row z pass needs P <= 32, 32 % P == 0 and a power-of-two row");
+    static_assert(N <= (NT ? C::WSTRIDE : WIN + RW * C::XROW), "warp area too small for the twiddle scratch");
+    extern __shared__ __align__(16) float2 sm[];
+    float2* twl = sm;                                  // [NTW][P] stage twiddles
+    float2* twp = twl + C::NTW * P;                    // [E][P] pack twiddles tw[p + P i]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane / P, p = lane - r * P;
+    {
+        float2* tw = sm + C::HDR + warp * (NT ? C::WSTRIDE : WIN + RW * C::XROW);   // scratch: this warp's area
+        if (warp == 0) {
+            for (int i = lane; i < N; i += 32) tw[i] = twg[i];
+            __syncwarp();
+            if (lane < P) {
+                fft_row_twiddles<M, N>(twl, tw, lane);
+#pragma unroll
+                for (int i = 0; i < E; ++i) twp[i * P + lane] = tw[lane + P * i];
+            }
+        }
+        __syncthreads();
+    }
+    float2* win = sm + C::HDR + warp * (NT ? C::WSTRIDE : WIN + RW * C::XROW);   // [RW][M] input rows
+    float2* wpt = win + WIN;                                                       // [MAXP][RW][M] partners
+    float2* xrow = win + WIN * (NT ? 1 + C::MAXP : 1) + r * C::XROW;                // this row's exchange buffer
+    const YZExpArgs& z = args.z;
+    const long long rows = (long long)N * N;
+    const long long groups = rows / RW;
+    const long long fstride2 = args.cells / 2;
+    for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups;
+         grp += (long long)gridDim.x * kRowWarps) {
+        const long long row0 = grp * RW, row = row0 + r;
+        float2 accA[NA][E], accB[NA][E];
+#pragma unroll
+        for (int t = 0; t < NA; ++t)
+#pragma unroll
+            for (int i = 0; i < E; ++i) accA[t][i] = accB[t][i] = make_float2(0.f, 0.f);
+        int cur = -1;
+        for (int f = 0; f < z.nout; ++f) {
+            const int code = z.codes[f];
+            const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
+            __syncwarp();                                  // earlier reads of win / wpt are done
+            int np = 0;
+            if constexpr (NT > 0) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    if (t >= args.ntargets) break;
+                    const PairTarget& T = args.t[t];
+                    for (int q = 0; q < T.pcount[slot]; ++q, ++np) {
+                        const float2* src = reinterpret_cast<const float2*>(T.partner) +
+                                            (long long)T.pfield[slot][q] * fstride2 + row0 * M;
+#pragma unroll
+                        for (int u = 0; u < WIN / 64; ++u)
+                            cp_async16(wpt + np * WIN + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
+                    }
+                }
+                cp_async_commit();
+            }
+            if (in != cur) {
+                const float4* src = reinterpret_cast<const float4*>(z.in + in * z.in_stride + row0 * M);
+                float4 v[WIN / 64];
+#pragma unroll
+                for (int u = 0; u < WIN / 64; ++u) v[u] = __ldg(src + lane + 32 * u);
+#pragma unroll
+                for (int u = 0; u < WIN / 64; ++u) reinterpret_cast<float4*>(win)[lane + 32 * u] = v[u];
+                __syncwarp();
+                cur = in;
+            }
+            const float2* colp = win + r * M;
+            float2 x[E];
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int k = p + P * i;
+                float2 Xk = colp[k];
+                float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
+                if (g) {
+                    const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
+                    Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);
+                    Xm = cscale(Xm, g == 1 ? k2 : k2 * k2);
+                }
+                if (cc == 1) {
+                    Xk = cmul_i<+1>(Xk);
+                    Xm = cmul_i<+1>(Xm);
+                } else if (cc == 2) {
+                    Xk = cmul_i<-1>(Xk);
+                    Xm = cmul_i<-1>(Xm);
+                }
+                Xm = cconj(Xm);
+                const float2 Ev = cadd(Xk, Xm);
+                const float2 Ov = cmul(csub(Xk, Xm), twp[i * P + p]);
+                x[i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
+            }
+            fft_row<M, +1>(x, p, xrow, twl);              // x[i]: real cells 2n, 2n + 1, n = p + P i
+            float2* dst = NT > 0 ? (args.store ? reinterpret_cast<float2*>(args.store) + slot * fstride2 : nullptr)
+                                 : z.out + slot * z.out_stride;
+            if (dst) {
+#pragma unroll
+                for (int i = 0; i < E; ++i) dst[row * M + p + P * i] = x[i];
+            }
+            if constexpr (NT > 0) {
+                cp_async_wait_all();
+                __syncwarp();                              // partner rows of every lane have landed
+                np = 0;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    if (t >= args.ntargets) break;
+                    const PairTarget& T = args.t[t];
+                    for (int q = 0; q < T.pcount[slot]; ++q, ++np) {
+                        const float ca = T.pcoef_a[slot][q], cb = T.pcoef_b[slot][q];
+                        const float2* pr = wpt + np * WIN + r * M;
+#pragma unroll
+                        for (int i = 0; i < E; ++i) {
+                            const float2 gv = pr[p + P * i];
+                            const float2 fg = make_float2(x[i].x * gv.x, x[i].y * gv.y);
+                            accA[t][i].x = fmaf(ca, fg.x, accA[t][i].x);
+                            accA[t][i].y = fmaf(ca, fg.y, accA[t][i].y);
+                            accB[t][i].x = fmaf(cb, fg.x, accB[t][i].x);
+                            accB[t][i].y = fmaf(cb, fg.y, accB[t][i].y);
+                        }
+                    }
+                }
+            }
+        }
+        if constexpr (NT > 0) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                if (t >= args.ntargets) break;
+                const PairTarget& T = args.t[t];
+                if (T.acc_in_a) {
+                    const float2* ia = reinterpret_cast<const float2*>(T.acc_in_a) + row * M;
+                    const float2* ib = reinterpret_cast<const float2*>(T.acc_in_b) + row * M;
+#pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        const float2 va = __ldg(ia + p + P * i), vb = __ldg(ib + p + P * i);
+                        accA[t][i].x += va.x;
+                        accA[t][i].y += va.y;
+                        accB[t][i].x += vb.x;
+                        accB[t][i].y += vb.y;
+                    }
+                }
+                float2* oa = reinterpret_cast<float2*>(T.out_a) + row * M;
+                float2* ob = reinterpret_cast<float2*>(T.out_b) + row * M;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    oa[p + P * i] = make_float2(fmaf(T.ca0, accA[t][i].x, T.ca1 * accB[t][i].x),
+                                                fmaf(T.ca0, accA[t][i].y, T.ca1 * accB[t][i].y));
+                    ob[p + P * i] = make_float2(fmaf(T.cb0, accA[t][i].x, T.cb1 * accB[t][i].x),
+                                                fmaf(T.cb0, accA[t][i].y, T.cb1 * accB[t][i].y));
+                }
+            }
         }
     }
 }
@@ -911,6 +1108,30 @@ struct Launch {
         }
         return cudaGetLastError();
     }
+    // warp-row z pass (store only for NT = 0); persistent grid of resident blocks
+    template <int NT>
+    static cudaError_t zrow(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
+        using C = RowCfg<N>;
+        if constexpr (!C::ok) {
+            return cudaErrorNotSupported;
+        } else {
+            const size_t smem = C::smem(NT);
+            cudaError_t e = set_smem(k_zrow<N, NT>, smem);
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0, per = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow<N, NT>, kRowWarps * 32, smem)) !=
+                cudaSuccess)
+                return e;
+            const long long groups = (long long)N * N / C::RW;
+            const long long need = (groups + kRowWarps - 1) / kRowWarps;
+            const long long resident = (long long)(per > 0 ? per : 1) * sms;
+            k_zrow<N, NT><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
+                a, g.tw, (float)g.kF);
+            return cudaGetLastError();
+        }
+    }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
     static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, double* partial,
                               cudaStream_t s) {
@@ -950,11 +1171,19 @@ struct Launch {
                       : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                              \
     }                                                                                                      \
     cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
-        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<true>(g, a, s)                     \
-                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<false>(g, a, s);                   \
+        if (v == 2 && RowCfg<N>::ok) {                                                                    \
+            ZPairArgs za{};                                                                                \
+            za.z = a;                                                                                      \
+            return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zrow<0>(g, za, s);                      \
+        }                                                                                                  \
+        return v == 1 ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<true>(g, a, s)                \
+                      : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zexp<false>(g, a, s);              \
     }                                                                                                      \
     int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
     cudaError_t transform_zexp_pairs_##N(const Geo& g, const ZPairArgs& a, cudaStream_t s) {               \
+        if (g.var[TV_ZEXP] == 2 && RowCfg<N>::ok)                                                          \
+            return a.ntargets <= 1 ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zrow<1>(g, a, s)        \
+                                   : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zrow<2>(g, a, s);       \
         return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZP>::zexp_pairs(g, a, s);                                 \
     }                                                                                                      \
     cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band, int nf,       \

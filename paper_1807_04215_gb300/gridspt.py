@@ -158,7 +158,7 @@ def check(plan):
 
 
 def autotune(plan, scratch=None):
-    """Time both tile variants of every transform pass and keep the faster;
+    """Time the tile variants of every transform pass and keep the fastest;
     returns the choices [column pass, x, y, z expansion, z forward]."""
     b = ctypes.c_size_t()
     _lib.check("gridspt_autotune_scratch_size", plan.lib.gridspt_autotune_scratch_size(plan.handle, ctypes.byref(b)))

@@ -221,6 +221,29 @@ def test_resume_equals_full_run_bitwise():
     assert torch.equal(full, part)
 
 
+def test_eighth_order_matches_oracle():
+    """Highest supported order (n_max = 8): orders 5..8 run pair launches whose
+    targets are split so that no output has more than three partner fields."""
+    errs = _parity_case(48, 300.0, 8, 41)
+    for (n, which), e in errs.items():
+        assert e < (1e-5 if n == 2 else 1e-4), (n, which, e)
+
+
+@pytest.mark.parametrize("start", [5, 7])
+def test_resume_at_high_order_equals_full_run_bitwise(start):
+    """Resuming at order 7 of n_max = 8 leaves only targets fed by two higher
+    orders (j >= 2) in the first pair launches of order 5: they must be split
+    over two launches."""
+    N, L, n_max = 32, 200.0, 8
+    plan = g.Plan(N, n_max, L)
+    d1 = g.make_linear_field(plan, [78])
+    full = g.run_orders(plan, d1)
+    part = full.clone()
+    part[:, start - 2:] = 0
+    g.run_orders(plan, d1, start_order=start, spectra=part)
+    assert torch.equal(full, part)
+
+
 def test_run_is_bitwise_repeatable_and_batched_equals_single():
     N, L, n_max = 48, 300.0, 4
     plan2 = g.Plan(N, n_max, L, batch=2)
