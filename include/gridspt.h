@@ -207,14 +207,16 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
  * 4 contiguous-axis forward pass) has two variants for N >= 128 (identical for
  * smaller N). The y expansion has a third, TMA-staged one (N >= 128). The z
- * expansion (with the fused pair products of the recursion) has a third that
- * runs one z row per warp without block-wide barriers (power-of-two N <= 512;
- * other sizes run variant 0 when it is chosen). gridspt_autotune times the
+ * expansion and the contiguous-axis forward pass have a third that runs one z
+ * row per group of warp lanes without block-wide barriers (power-of-two
+ * N <= 512; other sizes run variant 0 when it is chosen); the z expansion's
+ * choice also applies to the pair products fused into it and to the z pass of
+ * the bispectrum shells. gridspt_autotune times the
  * variants of every pass on `scratch` (device, >= gridspt_autotune_scratch_size
  * bytes, contents overwritten) with CUDA events on `stream`, keeps the fastest
  * in the plan and writes the choices to choices_out (host int32[5], may be
  * NULL). It synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning
- * store and read the choices (0 or 1; 0..2 for the y and z expansions), e.g.
+ * store and read the choices (0 or 1; 0..2 for passes 2, 3 and 4), e.g.
  * from a cache kept by the caller.
  * Results are bitwise identical for all variants: they only change how
  * columns and rows are grouped into thread blocks and warps. */

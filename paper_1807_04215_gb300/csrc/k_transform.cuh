@@ -615,6 +615,19 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
+// Lane-major twiddle tables of a warp-row kernel from the global table of
+// N-th roots (values identical to the tile kernels' shared copy).
+template <int N>
+__device__ __forceinline__ void zrow_tables(float2* twl, float2* twp, const float2* __restrict__ twg) {
+    using C = RowCfg<N>;
+    if (threadIdx.x < C::P) {
+        fft_row_twiddles<C::M, N>(twl, twg, threadIdx.x);
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) twp[i * C::P + threadIdx.x] = twg[threadIdx.x + C::P * i];
+    }
+    __syncthreads();
+}
+
 template <int N, int NT>
 __global__ void __launch_bounds__(kRowWarps * 32, 2)
 k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
@@ -622,25 +635,12 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW, WIN = C::WIN;
     constexpr int NA = NT > 0 ? NT : 1;
     static_assert(C::ok, "warp-row z pass needs P <= 32, 32 % P == 0 and a power-of-two row");
-    static_assert(N <= (NT ? C::WSTRIDE : WIN + RW * C::XROW), "warp area too small for the twiddle scratch");
     extern __shared__ __align__(16) float2 sm[];
     float2* twl = sm;                                  // [NTW][P] stage twiddles
     float2* twp = twl + C::NTW * P;                    // [E][P] pack twiddles tw[p + P i]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane / P, p = lane - r * P;
-    {
-        float2* tw = sm + C::HDR + warp * (NT ? C::WSTRIDE : WIN + RW * C::XROW);   // scratch: this warp's area
-        if (warp == 0) {
-            for (int i = lane; i < N; i += 32) tw[i] = twg[i];
-            __syncwarp();
-            if (lane < P) {
-                fft_row_twiddles<M, N>(twl, tw, lane);
-#pragma unroll
-                for (int i = 0; i < E; ++i) twp[i * P + lane] = tw[lane + P * i];
-            }
-        }
-        __syncthreads();
-    }
+    zrow_tables<N>(twl, twp, twg);
     float2* win = sm + C::HDR + warp * (NT ? C::WSTRIDE : WIN + RW * C::XROW);   // [RW][M] input rows
     float2* wpt = win + WIN;                                                       // [MAXP][RW][M] partners
     float2* xrow = win + WIN * (NT ? 1 + C::MAXP : 1) + r * C::XROW;                // this row's exchange buffer
@@ -905,6 +905,11 @@ __device__ __forceinline__ void kahan_add2(float& s, float& c, float x) {
     c = (t - s) - y;
     s = t;
 }
+// a^2 b summed over the two cells of a float2, with explicit roundings (no
+// contraction), so that every shell kernel forms bitwise the same terms
+__device__ __forceinline__ float cell_sq_mul(float2 a, float2 b) {
+    return __fadd_rn(__fmul_rn(__fmul_rn(a.x, a.x), b.x), __fmul_rn(__fmul_rn(a.y, a.y), b.y));
+}
 
 template <int N, int TZ, int NF>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
@@ -914,7 +919,8 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* t3 = sm + N;
-    __shared__ double r1[32], r2[32];
+    __shared__ double r1[TZ], r2[TZ];
+    static_assert(NT % 32 == 0, "block of whole warps");
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
     const long long rows = (long long)N * N;
@@ -957,35 +963,161 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     if (row0 + c < rows) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            const float2 a = x[0][i], b = x[1][i];   // cells 2n, 2n + 1
-            kahan_add2(s1, c1, a.x * a.x * b.x + a.y * a.y * b.y);
-            if constexpr (NF == 3) {
-                const float2 j = x[NF - 1][i];
-                kahan_add2(s2, c2, j.x * j.x * j.x + j.y * j.y * j.y);
-            }
+            kahan_add2(s1, c1, cell_sq_mul(x[0][i], x[1][i]));            // cells 2n, 2n + 1
+            if constexpr (NF == 3) kahan_add2(s2, c2, cell_sq_mul(x[NF - 1][i], x[NF - 1][i]));
         }
     }
-    double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
-    // fixed-order reduction: warp shuffles, then warps in order
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        d1 += __shfl_down_sync(0xffffffffu, d1, off);
-        d2 += __shfl_down_sync(0xffffffffu, d2, off);
-    }
+    const double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
+    // fixed-order reduction, grouped as in the warp-row kernel: per row a
+    // shuffle tree over its P threads, then the block's rows in order
+    __syncthreads();                                   // tiles are no longer read
+    double* red = reinterpret_cast<double*>(t3);       // [2][TZ][P]
+    red[c * P + p] = d1;
+    red[NT + c * P + p] = d2;
+    __syncthreads();
     const int w = tid >> 5, lane = tid & 31;
-    if (lane == 0) {
-        r1[w] = d1;
-        r2[w] = d2;
+    for (int rr = w; rr < TZ; rr += NT / 32 > 0 ? NT / 32 : 1) {
+        double a = lane < P ? red[rr * P + lane] : 0.0, b = lane < P ? red[NT + rr * P + lane] : 0.0;
+        for (int q = lane + 32; q < P; q += 32) {     // rows longer than a warp (P = 64)
+            a += red[rr * P + q];
+            b += red[NT + rr * P + q];
+        }
+#pragma unroll
+        for (int off = (P < 32 ? P : 32) / 2; off > 0; off >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, off);
+            b += __shfl_down_sync(0xffffffffu, b, off);
+        }
+        if (lane == 0) {
+            r1[rr] = a;
+            r2[rr] = b;
+        }
     }
     __syncthreads();
     if (tid == 0) {
         double a = 0.0, b = 0.0;
-        for (int i = 0; i < NT / 32; ++i) {
+        for (int i = 0; i < TZ; ++i) {
             a += r1[i];
             b += r2[i];
         }
         partial[2 * blockIdx.x] = a;
         partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// Warp-row form of k_zshell: one z row per P lanes, the band-limited inputs
+// (kz < band) read straight into registers by coalesced loads, the transform
+// exchanged through a per-warp buffer. Each warp sums a group of G = TZZ0
+// consecutive rows (G is the tile kernel's block height): per-lane Kahan sums,
+// a shuffle tree over the row's P lanes, rows added in order, one FP64
+// partial pair per group. Terms, tree and order are those of the tile kernel,
+// so the partials are bitwise equal.
+template <int N, int NF>
+__global__ void __launch_bounds__(kRowWarps * 32, 2)
+k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
+             double* __restrict__ partial) {
+    using C = RowCfg<N>;
+    constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW;
+    constexpr int G = Cfg<N>::TZZ0;
+    static_assert(C::ok && G % RW == 0, "warp-row shell pass: whole rows per warp and per group");
+    extern __shared__ __align__(16) float2 sm[];
+    float2* twl = sm;
+    float2* twp = twl + C::NTW * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane / P, p = lane - r * P;
+    zrow_tables<N>(twl, twp, twg);
+    float2* xrow = sm + C::HDR + (warp * RW + r) * C::XROW;
+    const int B = band < M ? band : M;
+    const long long groups = (long long)N * N / G;
+    for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups;
+         grp += (long long)gridDim.x * kRowWarps) {
+        double acc1 = 0.0, acc2 = 0.0;
+        for (int rr = 0; rr < G; rr += RW) {
+            const long long row = grp * G + rr + r;
+            float2 x[NF][E];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const float2* src = in + f * in_stride + row * M;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int k = p + P * i;
+                    const float2 Xk = k < B ? __ldg(src + k) : make_float2(0.f, 0.f);
+                    const float2 Xm = k ? cconj(M - k < B ? __ldg(src + M - k) : make_float2(0.f, 0.f))
+                                        : make_float2(0.f, 0.f);
+                    const float2 Ev = cadd(Xk, Xm);
+                    const float2 Ov = cmul(csub(Xk, Xm), twp[i * P + p]);
+                    x[f][i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) fft_row<M, +1>(x[f], p, xrow, twl);
+            float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                kahan_add2(s1, c1, cell_sq_mul(x[0][i], x[1][i]));
+                if constexpr (NF == 3) kahan_add2(s2, c2, cell_sq_mul(x[NF - 1][i], x[NF - 1][i]));
+            }
+            double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
+#pragma unroll
+            for (int off = P / 2; off > 0; off >>= 1) {
+                d1 += __shfl_down_sync(0xffffffffu, d1, off);
+                d2 += __shfl_down_sync(0xffffffffu, d2, off);
+            }
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {                 // the warp's rows in order
+                acc1 += __shfl_sync(0xffffffffu, d1, q * P);
+                acc2 += __shfl_sync(0xffffffffu, d2, q * P);
+            }
+        }
+        if (lane == 0) {
+            partial[2 * grp] = acc1;
+            partial[2 * grp + 1] = acc2;
+        }
+    }
+}
+
+// Warp-row form of k_zr2c (forward z pass of `count` fields, in place
+// allowed): each warp reads its rows into registers, transforms them, and
+// forms the half spectrum from the exchange buffer; arithmetic per element is
+// that of k_zr2c, so results are bitwise equal.
+template <int N>
+__global__ void __launch_bounds__(kRowWarps * 32, 2)
+k_zrow_r2c(const float2* in, float2* out, long long fstride, int count, const float2* __restrict__ twg,
+           float scale) {
+    using C = RowCfg<N>;
+    constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW;
+    static_assert(C::ok, "warp-row z pass needs P <= 32, 32 % P == 0 and a power-of-two row");
+    extern __shared__ __align__(16) float2 sm[];
+    float2* twl = sm;
+    float2* twp = twl + C::NTW * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane / P, p = lane - r * P;
+    zrow_tables<N>(twl, twp, twg);
+    float2* xrow = sm + C::HDR + (warp * RW + r) * C::XROW;
+    const long long per = (long long)N * N / RW;        // row groups per field
+    const long long groups = per * count;
+    const float half = 0.5f * scale;
+    for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups;
+         grp += (long long)gridDim.x * kRowWarps) {
+        const long long fld = grp / per, row = (grp - fld * per) * RW + r;
+        const float2* src = in + fld * fstride + row * M;
+        float2* dst = out + fld * fstride + row * M;
+        float2 x[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = src[p + P * i];
+        fft_row<M, -1>(x, p, xrow, twl);
+#pragma unroll
+        for (int i = 0; i < E; ++i) xrow[xpad(p + P * i)] = x[i];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = p + P * i;
+            const float2 Z = xrow[xpad(k)];
+            const float2 Zr = cconj(xrow[xpad(k ? M - k : 0)]);
+            const float2 S = cadd(Z, Zr);                            // 2 E[k]
+            const float2 t = cmul(cconj(twp[i * P + p]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
+            dst[k] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
+        }
+        __syncwarp();                                    // exchange buffer free for the next row
     }
 }
 
@@ -1021,6 +1153,29 @@ struct Launch {
         }
         GRIDSPT_COL(1, false)
 #undef GRIDSPT_COL
+    }
+    static cudaError_t zrow_r2c(const Geo& g, const float2* in, float2* out, long long fs, int count, float scale,
+                                cudaStream_t s) {
+        using C = RowCfg<N>;
+        if constexpr (!C::ok) {
+            return cudaErrorNotSupported;
+        } else {
+            const size_t smem = sizeof(float2) * (C::HDR + (size_t)kRowWarps * C::RW * C::XROW);
+            cudaError_t e = set_smem(k_zrow_r2c<N>, smem);
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0, per = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow_r2c<N>, kRowWarps * 32, smem)) !=
+                cudaSuccess)
+                return e;
+            const long long groups = (long long)N * N / C::RW * count;
+            const long long need = (groups + kRowWarps - 1) / kRowWarps;
+            const long long resident = (long long)(per > 0 ? per : 1) * sms;
+            k_zrow_r2c<N><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
+                in, out, fs, count, g.tw, scale);
+            return cudaGetLastError();
+        }
     }
     static cudaError_t zr2c(const Geo& g, const float2* in, float2* out, long long fs, int count,
                             float scale, cudaStream_t s) {
@@ -1133,8 +1288,34 @@ struct Launch {
         }
     }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
+    template <int NF>
+    static cudaError_t zrow_shell(const Geo& g, const float2* in, long long st, int band, double* partial,
+                                  cudaStream_t s) {
+        using C = RowCfg<N>;
+        if constexpr (!C::ok) {
+            return cudaErrorNotSupported;
+        } else {
+            const size_t smem = sizeof(float2) * (C::HDR + (size_t)kRowWarps * C::RW * C::XROW);
+            cudaError_t e = set_smem(k_zrow_shell<N, NF>, smem);
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0, per = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow_shell<N, NF>, kRowWarps * 32,
+                                                                     smem)) != cudaSuccess)
+                return e;
+            const long long groups = (long long)N * N / Cfg<N>::TZZ0;
+            const long long need = (groups + kRowWarps - 1) / kRowWarps;
+            const long long resident = (long long)(per > 0 ? per : 1) * sms;
+            k_zrow_shell<N, NF><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
+                in, st, band, g.tw, partial);
+            return cudaGetLastError();
+        }
+    }
     static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, double* partial,
                               cudaStream_t s) {
+        if (g.var[TV_ZEXP] == 2 && RowCfg<N>::ok && TZZ == Cfg<N>::TZZ0)
+            return nf == 3 ? zrow_shell<3>(g, in, st, band, partial, s) : zrow_shell<2>(g, in, st, band, partial, s);
         const size_t smem = sizeof(float2) * (N + (size_t)nf * TZZ * PITCH);
         cudaError_t e;
         if (nf == 3) {
@@ -1158,6 +1339,8 @@ struct Launch {
     }                                                                                                      \
     cudaError_t transform_zr2c_##N(const Geo& g, const float2* in, float2* out, long long fs, int count,   \
                                    float scale, int v, cudaStream_t s) {                                   \
+        if (v == 2 && RowCfg<N>::ok)                                                                       \
+            return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zrow_r2c(g, in, out, fs, count, scale, s);        \
         return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ1>::zr2c(g, in, out, fs, count, scale, s)            \
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zr2c(g, in, out, fs, count, scale, s);           \
     }                                                                                                      \

@@ -45,14 +45,14 @@ def test_mixed_size_batch_one_launch_equals_separate_runs():
 @pytest.mark.parametrize("N,n_max", [(32, 5), (64, 5), (128, 3), (192, 5), (256, 5), (512, 5)])
 def test_tile_variants_give_identical_results(N, n_max):
     """Tile widths, cp.async prefetch, the TMA-staged y pass (y variant 2) and
-    the warp-row z pass (z variant 2: one row per 2 .. 32 lanes for
-    power-of-two N, the tile kernel for N = 192) only regroup work: results are
-    bit-identical. n_max = 5 runs the z pass store-only, with one target and
-    with two targets."""
+    the warp-row z passes (z expansion and z forward variant 2: one row per
+    2 .. 32 lanes for power-of-two N, the tile kernels for N = 192) only
+    regroup work: results are bit-identical. n_max = 5 runs the z expansion
+    store-only, with one target and with two targets."""
     plan = g.Plan(N, n_max, 4.0 * N)
     d1 = g.make_linear_field(plan, [5])
     results = []
-    for choice in ([0] * 5, [1] * 5, [0, 0, 2, 0, 0], [0, 0, 0, 2, 0], [1, 1, 2, 2, 1]):
+    for choice in ([0] * 5, [1] * 5, [0, 0, 2, 0, 0], [0, 0, 0, 2, 0], [0, 0, 0, 0, 2], [1, 1, 2, 2, 2]):
         g.set_tuning(plan, choice)
         assert g.get_tuning(plan) == choice
         results.append(g.run_orders(plan, d1).clone())
@@ -62,8 +62,29 @@ def test_tile_variants_give_identical_results(N, n_max):
         assert torch.equal(ref, r)
     del results
     ch = g.autotune(plan)
-    assert len(ch) == 5 and all(0 <= c < k for c, k in zip(ch, (2, 2, 3, 3, 2)))
+    assert len(ch) == 5 and all(0 <= c < k for c, k in zip(ch, (2, 2, 3, 3, 3)))
     assert g.get_tuning(plan) == ch
     assert torch.equal(g.run_orders(plan, d1), ref)
     del ref
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("N", [32, 64, 256])
+def test_bispectrum_identical_for_warp_row_z_pass(N):
+    """The bispectrum's z pass in warp-row form (z expansion variant 2) forms
+    the same terms, per-row shuffle trees and row order as the tile kernel:
+    E and N_tri are bitwise equal, with and without the cached J^3 sums."""
+    L = 4.0 * N
+    kc = 2 * np.pi / L * N / 6
+    edges = [kc * i / 8 for i in range(9)]
+    out = []
+    for choice in ([0] * 5, [0, 0, 0, 2, 0]):
+        plan = g.Plan(N, 5, L)
+        g.set_tuning(plan, choice)
+        d1 = g.make_linear_field(plan, [9])
+        sp = g.run_orders(plan, d1)
+        first = g.bispectrum(plan, d1[0], sp[0, 0, 0], edges)       # J^3 formed
+        second = g.bispectrum(plan, d1[0], sp[0, 0, 0], edges)      # J^3 from the cache
+        out.append([t.clone() for t in first] + [t.clone() for t in second])
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
