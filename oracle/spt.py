@@ -179,6 +179,60 @@ def run_orders(delta1_k, L, n_max, kcut_nl=None):
     return delta, theta
 
 
+def run_orders_divergence(delta1_k, L, n_max, kcut_nl=None):
+    """Eq. recursion_formula with its sources rewritten in divergence form.
+
+    With u = grad nabla^-2 theta (Eq. u_and_theta), theta = div u and u curl free:
+        grad delta_m . u_r + delta_m theta_r = div (delta_m u_r),
+        sum over the ordered pairs (m, r) of [d_j u_{m,k} d_k u_{r,j} + u_m . grad theta_r]
+            = (1/2) nabla^2 sum_m u_m . u_{n-m},
+    so A_n = div V_n and B_n = (1/2) nabla^2 S_n with V_n = sum_m delta_m u_{n-m},
+    S_n = sum_m u_m . u_{n-m} formed cell by cell. V_n and S_n are transformed
+    forward, A_n(k) = i k . V_n(k) and B_n(k) = -(k^2 / 2) S_n(k) taken in
+    k-space, and delta_n, theta_n follow from the same 2x2 recursion. Modes
+    |k| < k_cut of delta_1's cut agree with ``run_orders`` to rounding (the
+    identities hold exactly for products that do not fold); above it the
+    folded parts of the products differ between the two forms.
+    Returns (delta_k, theta_k) lists indexed by order like ``run_orders``."""
+    N = delta1_k.shape[0]
+    kF = 2.0 * math.pi / L
+    nyq = nyquist_mask(N)
+    sx, sy, sz = wave_indices(N)
+    s2 = (sx * sx + sy * sy + sz * sz).astype(np.float64)
+    kv = [kF * sx, kF * sy, kF * sz]
+    k2 = kv[0] ** 2 + kv[1] ** 2 + kv[2] ** 2
+    inv_k2 = np.zeros_like(k2)
+    inv_k2[k2 > 0] = 1.0 / k2[k2 > 0]
+    delta = [None, delta1_k.copy()]
+    theta = [None, delta1_k.copy()]          # Eq. recursion_n=1
+    d_x, u_x = {}, {}
+    for n in range(2, n_max + 1):
+        m = n - 1
+        d_x[m] = to_real(backward(delta[m]), "delta")
+        u_x[m] = [to_real(backward(-1j * kv[a] * inv_k2 * theta[m]), "u") for a in range(3)]
+        V = [0.0, 0.0, 0.0]
+        S = 0.0
+        for m in range(1, n):
+            r = n - m
+            for a in range(3):
+                V[a] = V[a] + d_x[m] * u_x[r][a]
+                S = S + u_x[m][a] * u_x[r][a]
+        A = sum(1j * kv[a] * forward(V[a]) for a in range(3))
+        B = -0.5 * k2 * forward(S)
+        cdA, cdB, ctA, ctB = recursion_coefficients(n)
+        dn = cdA * A + cdB * B
+        tn = ctA * A + ctB * B
+        dn[nyq] = 0.0
+        tn[nyq] = 0.0
+        if kcut_nl is not None and kcut_nl > 0:
+            rr = kcut_nl * L / (2.0 * math.pi)
+            dn[s2 > rr * rr] = 0.0
+            tn[s2 > rr * rr] = 0.0
+        delta.append(dn)
+        theta.append(tn)
+    return delta, theta
+
+
 def real_space_orders(delta1_k, L, n_max, kcut_nl=None):
     """delta_n(x) and theta_n(x) as formed by the recursion before the forward
     transform (step (3)/(6) output), for n = 2..n_max."""

@@ -6,8 +6,12 @@ the rules: nothing computed by the GPU is fed to the oracle).
   RMS relative error per order (all modes, in band |k| < K_c, above band) and
   per-bin error of the six P-terms, printed as one report line.
 * 1024^3, L = 4000 Mpc/h, n_max = 5 (about 250 GB of device memory; runs only
-  with GRIDSPT_LARGE=1): mass conservation delta_n(0) ~ 0, exact 2^n scaling,
-  and P11 against the linear spectrum within its cosmic variance.
+  with GRIDSPT_LARGE=1): delta_2, theta_2 on an 8^3 block of cells against the
+  oracle's direct FP64 mode sums from its own delta_1 (oracle/cutout.py),
+  mass conservation delta_n(0) ~ 0, exact 2^n scaling, and P11 against the
+  linear spectrum within its cosmic variance. Orders above 2 would need the
+  full-grid lower orders in FP64 (or GPU fields as oracle input, which the
+  rules exclude); their accumulated error is measured by the 128^3 rerun.
 """
 import json
 import math
@@ -20,7 +24,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from oracle import cosmology, estimators, spt  # noqa: E402
+from oracle import cosmology, cutout, estimators, spt  # noqa: E402
 from paper_1807_04215_gb300 import gridspt as g  # noqa: E402
 from tests import inputs  # noqa: E402
 
@@ -97,6 +101,22 @@ def test_1024_properties():
         del a2
         rep["mass"][n] = float(f"{z / rms_cell:.2e}")
         assert z <= 16 * 2.0 ** -24 * rms_cell
+    # n = 2 on an 8^3 block of cells against the oracle's direct FP64 mode sums
+    # (its own delta_1 drawn mode by mode; nothing from the GPU run): RMS relative
+    # error over the block, same bound as the field parity at n = 2
+    sx, sy, sz, v = cutout.linear_modes(N, L, n_max, cosmology.DEFAULT_COSMO, 1000)
+    origin = (300, 611, 17)
+    d2o, t2o = cutout.second_order_at_block(sx, sy, sz, v, N, L, origin, size=8)
+    del sx, sy, sz, v
+    rep["cutout_n2"] = {}
+    for which, ref in ((0, d2o), (1, t2o)):
+        x = g.c2r(plan, sp[0, 0, which])
+        blk = x[origin[0]:origin[0] + 8, origin[1]:origin[1] + 8, origin[2]:origin[2] + 8].double().cpu().numpy()
+        del x
+        rel = float(np.sqrt(np.mean((blk - ref) ** 2) / np.mean(ref ** 2)))
+        rep["cutout_n2"]["delta_2" if which == 0 else "theta_2"] = float(f"{rel:.2e}")
+        assert rel < 1e-5, (which, rel)
+    torch.cuda.empty_cache()
     # exact 2^n scaling (every step is linear or a product; scaling by 2 is exact)
     # (a second spectra buffer does not fit beside the workspace: a slab of 16 kx
     # planes of every order is kept and compared bitwise)

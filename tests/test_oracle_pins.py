@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 from scipy import integrate
 
-from oracle import cosmology, estimators, kernels, rng, spt
+from oracle import cosmology, cutout, estimators, kernels, rng, spt
 from tests import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -414,3 +414,84 @@ def test_bf16_rounding_ties_and_range():
     assert mlp.bf16_round(np.array([1.0 + 2.0 ** -7]))[0] == 1.0 + 2.0 ** -7
     x = inputs.rng(1).standard_normal(1000)
     assert np.max(np.abs(mlp.bf16_round(x) / x - 1)) <= 2.0 ** -8
+
+
+# ------------------------------------------------------- block evaluation (cutout)
+def test_cutout_modes_equal_full_grid_draw():
+    """The in-band canonical modes drawn one by one equal the full-grid field
+    at those modes, and the grid holds nothing else (its other half is their
+    conjugates)."""
+    N, L, n_max, seed = 24, 150.0, 3, 17
+    full = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed)
+    sx, sy, sz, val = cutout.linear_modes(N, L, n_max, cosmology.DEFAULT_COSMO, seed)
+    assert np.array_equal(full[sx % N, sy % N, sz % N], val)
+    assert np.array_equal(full[-sx % N, -sy % N, -sz % N], np.conj(val))
+    assert np.count_nonzero(full) == 2 * val.size
+
+
+def test_cutout_second_order_plane_wave_closed_form():
+    """One wave delta_1 = A cos(k.x): delta_2 = theta_2 = A^2 cos(2 k.x) (the
+    Zel'dovich solution of a single wave), at a block that wraps around the box."""
+    N, L, A = 32, 100.0, 0.3
+    s = np.array([1]), np.array([2]), np.array([3])
+    d2, t2 = cutout.second_order_at_block(*s, np.array([A / 2 + 0j]), N, L, origin=(29, 5, 30), size=4)
+    a = (29 + np.arange(4)) % N
+    b = (5 + np.arange(4)) % N
+    c = (30 + np.arange(4)) % N
+    ph = 2 * math.pi * (a[:, None, None] + 2 * b[None, :, None] + 3 * c[None, None, :]) / N
+    exp = A * A * np.cos(2 * ph)
+    assert np.max(np.abs(d2 - exp)) < 1e-13
+    assert np.max(np.abs(t2 - exp)) < 1e-13
+
+
+def test_cutout_second_order_equals_full_grid_oracle():
+    """Direct mode sums at a block equal the full-grid recursion (FFT based) at
+    the same cells for a random band-limited field."""
+    N, L, n_max, seed = 16, 120.0, 5, 23
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, seed)
+    ref = spt.real_space_orders(d1, L, 2)[2]
+    sx, sy, sz, val = cutout.linear_modes(N, L, n_max, cosmology.DEFAULT_COSMO, seed)
+    origin = (13, 2, 9)
+    d2, t2 = cutout.second_order_at_block(sx, sy, sz, val, N, L, origin, size=6)
+    idx = [(o + np.arange(6)) % N for o in origin]
+    for got, full in ((d2, ref[0]), (t2, ref[1])):
+        want = full[np.ix_(*idx)]
+        assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+# ------------------------------------------------------ divergence-form sources
+def test_divergence_form_equals_direct_form_in_band():
+    """A_n = div V_n, B_n = (1/2) nabla^2 S_n is an exact rewriting of the
+    nine-term sources: modes below delta_1's cut agree to rounding at every
+    order; orders 2 and 3 (products spanning at most 3 K_c <= k_Ny at
+    n_max = 5) agree at every mode; delta_n(0) is exactly zero."""
+    N, L, n_max = 24, 150.0, 5
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, 5)
+    dk, tk = spt.run_orders(d1, L, n_max)
+    vk, wk = spt.run_orders_divergence(d1, L, n_max)
+    sx, sy, sz = spt.wave_indices(N)
+    r = spt.cut_ratio(N, L, n_max, None)
+    band = (sx * sx + sy * sy + sz * sz) < r * r
+    for n in range(2, n_max + 1):
+        for a, b in ((dk[n], vk[n]), (tk[n], wk[n])):
+            scale = np.abs(a[band]).max()
+            assert np.abs(a[band] - b[band]).max() <= 1e-13 * scale
+            if n <= 3:
+                assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+            assert b[0, 0, 0] == 0
+
+
+def test_divergence_form_single_plane_wave_all_orders():
+    """Zel'dovich closed form of one wave (no folding) in the divergence form."""
+    N, L, A = 32, 100.0, 0.1
+    d1 = inputs.plane_waves(N, [((1, 0, 0), A)])
+    dk, tk = spt.run_orders_divergence(d1, L, 5)
+    for n in range(2, 6):
+        exp = np.zeros((N, N, N), complex)
+        for m in range(n % 2, n + 1, 2):
+            j = (n - m) // 2
+            v = (-1) ** j * m ** n * (A / 2) ** n / (math.factorial(j) * math.factorial(m + j))
+            exp[m % N, 0, 0] = v
+            exp[-m % N, 0, 0] = v
+        assert np.abs(dk[n] - exp).max() < 1e-15
+        assert np.abs(tk[n] - exp).max() < 1e-15
