@@ -31,10 +31,12 @@ UNIT = "Mcells*orders/s"
 N_GRID, BOX, N_MAX = 512, 2000.0, 5
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic / algorithmic bytes measured by ncu for the kernels as they stand
-# (profiles/k_xexp_k_yexp_k_zexp_c2r-512.md: 512^3, one field per launch);
-# traffic per launch is reported as this ratio times the launch's algorithmic
-# bytes. A kernel changed since its capture has no entry (traffic null).
-NCU_TRAFFIC_RATIO = {"y_expand": 0.969, "x_expand": 0.966}
+# (profiles/k_xexp_k_yexp_k_zexp_c2r-512.md: 512^3, one field per launch;
+# profiles/k_zrow_orders-256.md: the warp-row z expansion, the four launches of
+# one realisation at 256^3, bytes growing as N^3); traffic per launch is
+# reported as this ratio times the launch's algorithmic bytes. A kernel changed
+# since its capture has no entry (traffic null).
+NCU_TRAFFIC_RATIO = {"y_expand": 0.969, "x_expand": 0.966, "z_expand": 1.003}
 
 
 def log_edges(lo, hi, nb):
@@ -276,6 +278,8 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     graph_ms = ev0.elapsed_time(ev1) / args.steps
     graph.close()
+    del ws
+    div = divergence_section(args, N, L, B, d1, spectra, stream) if rank == 0 else None
     mixed = mixed_batch(args) if rank == 0 and not args.quick else None
     emu = emulator_section(args) if rank == 0 and not args.quick else None
     if rank != 0:
@@ -318,6 +322,7 @@ def run_gpu(args, rank, world):
                             "unit": "Mcells*orders/s (orders 2..5, one graph launch, IC excluded)"},
         "mixed_batch": mixed,
         "emulator": emu,
+        "divergence_form": div,
     }
     # kernels launched per timed region: recorded launches plus the final-reduction kernels
     # of the estimators (one per power call and per bispectrum shell)
@@ -326,6 +331,55 @@ def run_gpu(args, rank, world):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def divergence_section(args, N, L, B, d1, spectra, stream):
+    """The same B realisations (orders 2..5, IC excluded) with the sources in
+    divergence form (A_n = div sum delta_m u_{n-m}, B_n = lap sum u_m . u_{n-m} / 2,
+    four real fields per order; not the paper's form, so not the headline), and
+    the RMS relative difference to the nine-term spectra on the modes below
+    delta_1's cut, where the two forms are equal up to rounding."""
+    import torch
+    from paper_1807_04215_gb300 import gridspt as g
+    plan = g.Plan(N, N_MAX, L, batch=B, form="divergence")
+    ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device="cuda")
+    tuning = g.autotune(plan, scratch=ws)
+    spd = torch.empty_like(spectra)
+    for _ in range(args.warmup):
+        g.run_orders(plan, d1, spectra=spd, ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.profile_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.run_orders(plan, d1, spectra=spd, ws=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = g.profile_end()
+    ms = e0.elapsed_time(e1) / args.steps
+    s = torch.arange(N, device="cuda")
+    s = torch.where(s < N // 2, s, s - N)
+    s2 = s[:, None, None] ** 2 + s[None, :, None] ** 2 + s[None, None, : N // 2] ** 2
+    band = (s2 < (N / (N_MAX + 1)) ** 2).to(torch.float64)
+    w = torch.full((N, N, N // 2), 2.0, dtype=torch.float64, device="cuda")
+    w[:, :, 0] = 1.0
+    w = w * band
+    worst = 0.0
+    for n in range(2, N_MAX + 1):
+        a, b = spectra[0, n - 2], spd[0, n - 2]
+        num = (w * (a - b).abs().double() ** 2).sum()
+        den = (w * a.abs().double() ** 2).sum()
+        worst = max(worst, float(torch.sqrt(num / den)))
+    gbytes = sum(v[2] for v in prof.values()) / args.steps / B / 1e9
+    del ws, spd
+    torch.cuda.empty_cache()
+    return {"ms_per_realisation": round(ms / B, 3), "realisations": B,
+            "value": round(B * N ** 3 * (N_MAX - 1) / ms / 1e3, 1),
+            "unit": "Mcells*orders/s (orders 2..5, IC excluded)",
+            "algorithmic_GB_per_realisation": round(gbytes, 2),
+            "avg_GBps": round(gbytes * B / (ms / 1e3), 1),
+            "autotune": tuning,
+            "in_band_rms_rel_vs_nine_term": float(f"{worst:.2e}")}
 
 
 def mixed_batch(args):

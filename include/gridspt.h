@@ -57,12 +57,24 @@ typedef enum {
 typedef struct gridspt_plan_s* gridspt_plan;
 typedef void* gridspt_stream; /* cudaStream_t */
 
+/* Form of the sources A_n, B_n of Eq. recursion_formula.
+ * GRIDSPT_FORM_NINE_TERM: the paper's bilinear terms, A_n = sum_m grad delta_m .
+ *   u_{n-m} + delta_m theta_{n-m}, B_n = sum_m d_j u_{m,k} d_k u_{n-m,j} +
+ *   u_m . grad theta_{n-m}, from 13 (order 1) or 17 real derived fields per order.
+ * GRIDSPT_FORM_DIVERGENCE: the same sources rewritten with theta = div u and u
+ *   curl free (Eq. u_and_theta): A_n = div sum_m delta_m u_{n-m}, B_n = (1/2)
+ *   lap sum_m u_m . u_{n-m}, the divergence and Laplacian taken in k-space; four
+ *   real fields per order (delta, u). Modes below delta_1's cut equal the
+ *   nine-term form's to rounding; modes above it, where the grid products fold,
+ *   differ between the two forms. Not in the paper. */
+enum { GRIDSPT_FORM_NINE_TERM = 0, GRIDSPT_FORM_DIVERGENCE = 1 };
+
 /* Problem description (Sec. II.C: box, grid, highest order, sharp-k cuts). */
 typedef struct {
     int32_t n;        /* grid points per side */
     int32_t n_max;    /* highest perturbative order, 1..8 */
     int32_t batch;    /* realisations per call of make_linear_field / run_orders */
-    int32_t reserved; /* must be 0 */
+    int32_t form;     /* GRIDSPT_FORM_NINE_TERM (default, 0) or GRIDSPT_FORM_DIVERGENCE */
     double box;       /* L in Mpc/h, > 0 */
     double kcut_lin;  /* sharp-k cut on delta_1 in h/Mpc (|k| <= kcut kept);
                          <= 0 selects 2 k_Ny / (n_max + 1), k_Ny = pi N / L */
@@ -84,9 +96,14 @@ gridspt_status gridspt_plan_create(const gridspt_desc* desc, gridspt_plan* out);
 /* Release the plan's device tables. Safe on NULL. Synchronises the device. */
 gridspt_status gridspt_plan_destroy(gridspt_plan plan);
 
-/* Bytes of caller workspace gridspt_run_orders needs: the real-space derived
- * fields of orders 1..n_max-1 (13 for order 1, 17 for each later order, Sec.
- * II.C steps (2) and (5)), 4 N^3 bytes each. Independent of batch. */
+/* Bytes of caller workspace gridspt_run_orders needs, in fields of 4 N^3 bytes
+ * (independent of batch). Nine-term form: the real-space derived fields (Sec.
+ * II.C steps (2) and (5)) of the orders m with 2m <= n_max (13 for order 1, 17
+ * for later orders; the pair products of the other orders are accumulated as
+ * soon as those are formed), two partial-sum fields per order n >= 4, and the
+ * expansion scratch of 19 fields: 53 fields for n_max = 5. Divergence form:
+ * delta and u of orders 1..n_max-1, the four source fields and 7 scratch
+ * fields: 4 n_max + 7 (27 for n_max = 5). */
 gridspt_status gridspt_workspace_size(gridspt_plan plan, size_t* bytes);
 
 /* Normalisation A of the linear spectrum (host only, FP64 Simpson in ln k). */

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <functional>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -154,6 +155,15 @@ int n_acc(int n_max) { return n_max >= 4 ? 2 * (n_max - 3) : 0; }
 int scratch_base(int n_max) { return acc_base(n_max) + n_acc(n_max); }
 int workspace_fields(int n_max) { return n_max >= 2 ? scratch_base(n_max) + kExpScratch : 0; }
 
+// Divergence-form workspace: the real fields delta, u_x, u_y, u_z of orders
+// 1..n_max-1 (every later order needs them), the sources V_x, V_y, V_z, S of
+// the order being formed (transformed in place), then the expansion scratch
+// (3 x-fields, 4 xy-fields).
+int div_order_base(int m) { return 4 * (m - 1); }
+int div_src_base(int n_max) { return 4 * (n_max - 1); }
+int div_scratch_base(int n_max) { return div_src_base(n_max) + 4; }
+int div_workspace_fields(int n_max) { return n_max >= 2 ? div_scratch_base(n_max) + 3 + 4 : 0; }
+
 // s2 threshold: smallest integer t >= 0 with kF * sqrt(t) >= e (FP64), so that
 // "t <= |s|^2" is exactly the FP64 test "e <= kF sqrt(|s|^2)".
 long long s2_threshold(double e, double kF) {
@@ -262,7 +272,9 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     if (d->n_max < 1 || d->n_max > kMaxOrder) return fail(GRIDSPT_E_INVALID, "n_max=%d outside [1, %d]", d->n_max, kMaxOrder);
     if (d->batch < 1) return fail(GRIDSPT_E_INVALID, "batch=%d < 1", d->batch);
     if (!(d->box > 0.0) || !std::isfinite(d->box)) return fail(GRIDSPT_E_INVALID, "box must be > 0");
-    if (d->reserved != 0) return fail(GRIDSPT_E_INVALID, "reserved field must be 0");
+    if (d->form != GRIDSPT_FORM_NINE_TERM && d->form != GRIDSPT_FORM_DIVERGENCE)
+        return fail(GRIDSPT_E_INVALID, "form=%d: must be GRIDSPT_FORM_NINE_TERM (0) or GRIDSPT_FORM_DIVERGENCE (1)",
+                    d->form);
     gridspt_plan_s* p = new (std::nothrow) gridspt_plan_s();
     if (!p) return fail(GRIDSPT_E_NOMEM, "host allocation failed");
     p->d = *d;
@@ -322,7 +334,8 @@ gridspt_status gridspt_plan_destroy(gridspt_plan p) {
 
 gridspt_status gridspt_workspace_size(gridspt_plan p, size_t* bytes) {
     if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
-    *bytes = (size_t)workspace_fields(p->d.n_max) * (size_t)field_floats(p) * sizeof(float);
+    const int nf = p->d.form == GRIDSPT_FORM_DIVERGENCE ? div_workspace_fields(p->d.n_max) : workspace_fields(p->d.n_max);
+    *bytes = (size_t)nf * (size_t)field_floats(p) * sizeof(float);
     return GRIDSPT_OK;
 }
 
@@ -614,6 +627,99 @@ gridspt_status backward_fields(const gridspt_plan_s* p, const float2* in0, const
 
 namespace {
 
+// Divergence form, one order m: the x pass (forward from the sources V, S when
+// `src` is set, writing delta_m(k), theta_m(k); else backward from the given
+// spectra) makes the x-fields delta, phi, kx phi (phi = theta / k^2); the y pass
+// the xy-fields delta, ky phi, phi, kx phi; the z pass stores delta and
+// u = -i k phi (Eq. u_and_theta) as real fields of order m. At m = n_max only
+// the forward x pass runs.
+gridspt_status derive_order_div(const gridspt_plan_s* p, int m, float2* dk, float2* tk, float* ws, const float2* src,
+                                cudaStream_t s) {
+    const long long F = field_c(p), cells = field_floats(p);
+    const double fb = 4.0 * (double)cells;
+    const int n_max = p->d.n_max;
+    float2* xs = reinterpret_cast<float2*>(ws + (long long)div_scratch_base(n_max) * cells);
+    float2* ys = xs + 3 * F;
+    XExpArgs xa{};
+    xa.src0 = dk;
+    xa.src1 = tk;
+    xa.out = xs;
+    xa.out_stride = F;
+    xa.s2_nl = p->s2_nl;
+    if (src) {
+        const double c = 2.0 / ((2.0 * m + 3.0) * (m - 1.0));   // Eq. recursion_formula (N^-3 is in the sources)
+        xa.fwd_first = 1;
+        xa.div_in = src;
+        xa.div_stride = F;
+        xa.cdA = (float)(c * (m + 0.5));
+        xa.cdB = (float)c;
+        xa.ctA = (float)(c * 1.5);
+        xa.ctB = (float)(c * m);
+    }
+    if (m < n_max) {
+        xa.nout = 3;
+        xa.codes[0] = x_code(XK_POW, 0, XS_DELTA);
+        xa.codes[1] = x_code(XK_POW, 0, XS_PHI);
+        xa.codes[2] = x_code(XK_POW, 1, XS_PHI);
+    }
+    const int nin = src ? 4 : (m == 1 ? 1 : 2);
+    CKP(src ? (m < n_max ? PK_XEXP_FWD : PK_X_FWD) : PK_XEXP, fb * (nin + (src ? 2 : 0) + xa.nout), s,
+        launch_xexp(p->geo, xa, s), "x pass (divergence form)");
+    if (m == n_max) return GRIDSPT_OK;
+    YZExpArgs ya{}, za{};
+    ya.in = xs;
+    ya.in_stride = F;
+    ya.out = ys;
+    ya.out_stride = F;
+    ya.nout = 4;
+    ya.codes[0] = y_code(0, 0, 0);   // delta
+    ya.codes[1] = y_code(1, 1, 1);   // ky phi
+    ya.codes[2] = y_code(1, 0, 2);   // phi
+    ya.codes[3] = y_code(2, 0, 3);   // kx phi
+    const int NI = 2;                // z-pass constant -i
+    za.in = ys;
+    za.in_stride = F;
+    za.out = reinterpret_cast<float2*>(ws + (long long)div_order_base(m) * cells);
+    za.out_stride = F;
+    za.nout = 4;
+    za.codes[0] = z_code(0, 0, 0, 0);    // delta
+    za.codes[1] = z_code(3, 0, NI, 1);   // u_x = -i kx phi
+    za.codes[2] = z_code(1, 0, NI, 2);   // u_y = -i ky phi
+    za.codes[3] = z_code(2, 1, NI, 3);   // u_z = -i kz phi
+    CKP(PK_YEXP, fb * (3 + 4), s, launch_yexp(p->geo, ya, s), "y expansion (divergence form)");
+    CKP(PK_ZEXP, fb * (4 + 4), s, launch_zexp(p->geo, za, s), "z expansion (divergence form)");
+    return GRIDSPT_OK;
+}
+
+// Orders 1..n_max of one realisation in divergence form (see derive_order_div).
+gridspt_status run_orders_div(const gridspt_plan_s* p, float2* d1, const std::function<float2*(int, int)>& spec,
+                              int start_order, float* w, cudaStream_t s) {
+    const int n_max = p->d.n_max;
+    const long long F = field_c(p), cells = field_floats(p);
+    const double fb = 4.0 * (double)cells;
+    float2* src = reinterpret_cast<float2*>(w + (long long)div_src_base(n_max) * cells);
+    for (int m = 1; m <= n_max; ++m) {
+        const bool given = m == 1 || m < start_order;
+        float2* dk = m == 1 ? d1 : spec(m, 0);
+        float2* tk = m == 1 ? d1 : spec(m, 1);
+        if (!given) {
+            ProductDivArgs pa{};
+            pa.ws = w;
+            pa.cells = cells;   // order q's fields at div_order_base(q) = 4 (q - 1)
+            pa.n = m;
+            pa.out = reinterpret_cast<float*>(src);
+            pa.scale = (float)(1.0 / (double)cells);
+            CKP(PK_PRODUCT, fb * 4.0 * m, s, launch_product_div(p->geo, pa, s), "divergence-form sources");
+            CKP(PK_ZR2C, 8 * fb, s, launch_zr2c(p->geo, src, src, F, 4, 1.0f, s), "z r2c (divergence form)");
+            CKP(PK_Y_FWD, 8 * fb, s, launch_colpass_fwd(p->geo, src, F, 4, 1, 0, -1, s), "y pass fwd (divergence form)");
+        } else if (m == n_max) {
+            break;
+        }
+        if (gridspt_status st = derive_order_div(p, m, dk, tk, w, given ? nullptr : src, s)) return st;
+    }
+    return GRIDSPT_OK;
+}
+
 gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t start_order, void* spectra,
                                void* ws, size_t ws_bytes, gridspt_stream stream) {
     if (check_plan(p)) return GRIDSPT_E_INVALID;
@@ -635,6 +741,10 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
         auto spec = [&](int n, int which) {
             return static_cast<float2*>(spectra) + ((long long)(b * (n_max - 1) + (n - 2)) * 2 + which) * F;
         };
+        if (p->d.form == GRIDSPT_FORM_DIVERGENCE) {
+            if (gridspt_status st = run_orders_div(p, d1, spec, start_order, w, s)) return st;
+            continue;
+        }
         std::vector<float2*> spec_delta(n_max + 1, nullptr);
         for (int n = 2; n <= n_max; ++n) spec_delta[n] = spec(n, 0);
         const double fb = 4.0 * (double)field_floats(p);

@@ -60,6 +60,13 @@ struct XExpArgs {
     long long shell_hi;
     int band;              // > 0: only columns with |ky| < band and kz < band are
                            //      transformed and written (all other outputs zero)
+    // divergence-form sources (fwd_first = 1): when div_in is set, the inputs are
+    // the y-transformed V_x, V_y, V_z, S at div_in + q * div_stride (q = 0..3);
+    // after the forward x transform A = i k . V, B = -(k^2 / 2) S and
+    // src0 = cdA A + cdB B, src1 = ctA A + ctB B are written (then finalised)
+    const float2* div_in;
+    long long div_stride;
+    float cdA, cdB, ctA, ctB;
 };
 
 struct YZExpArgs {
@@ -144,6 +151,18 @@ cudaError_t launch_colpass_fwd(const Geo& g, float2* data, long long fstride, in
 cudaError_t launch_zr2c(const Geo& g, const float2* in, float2* out, long long fstride, int count,
                         float scale, cudaStream_t s);
 cudaError_t launch_product(const Geo& g, const ProductArgs& a, cudaStream_t s);
+
+// Divergence-form sources of order n: V_n = sum_m delta_m u_{n-m} (3 fields) and
+// S_n = sum_m u_m . u_{n-m}, times `scale`, from the stored real fields of the
+// lower orders (order m: delta, u_x, u_y, u_z at ws + (4 (m - 1) + j) * cells).
+struct ProductDivArgs {
+    const float* ws;
+    long long cells;
+    int n;
+    float* out;            // V_x, V_y, V_z, S at out + q * cells
+    float scale;           // N^-3 (the forward transform is unnormalised)
+};
+cudaError_t launch_product_div(const Geo& g, const ProductDivArgs& a, cudaStream_t s);
 
 // Power: per-block partial sums (2 * nbins doubles per block) then a fixed-order
 // final reduction. blocks: number of partial-sum blocks (power_blocks()).

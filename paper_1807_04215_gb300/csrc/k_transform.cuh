@@ -215,7 +215,13 @@ k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restric
 // y-transformed product output: they are transformed forward along x and
 // finalised (delta_n(k), theta_n(k) complete, stored back in place), so the
 // spectra are read from HBM once for both directions.
-template <int N, int TZ, bool FWD>
+//
+// MODE 0: backward x pass only; MODE 1: forward first (FWD above); MODE 2:
+// forward first from the divergence-form sources: the four y-transformed
+// fields V_x, V_y, V_z, S are transformed forward along x and combined into
+// A = i k . V, B = -(k^2 / 2) S, delta = cdA A + cdB B, theta = ctA A + ctB B
+// (written to src0, src1 and finalised like MODE 1).
+template <int N, int TZ, int MODE>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PC)
 k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
@@ -233,17 +239,49 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
     const long long colofs = (long long)ky * M + kz;
     const bool two = args.src1 != args.src0;
     float2 xd[E], xt[E];
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-        xd[i] = act ? args.src0[colofs + (p + P * i) * estride] : make_float2(0.f, 0.f);
-        xt[i] = (act && two) ? args.src1[colofs + (p + P * i) * estride] : xd[i];
-    }
-    __syncthreads();
     const int sy = signed_idx(ky, N), sz = kz;
     const int syz = sy * sy + sz * sz;
-    if constexpr (FWD) {
-        fft_column<N, -1, N>(xd, p, buf + c, TZ, tw);
-        if (two) fft_column<N, -1, N>(xt, p, buf + c, TZ, tw);
+    if constexpr (MODE == 2) {
+        __syncthreads();                                  // twiddle table loaded
+        float2 A[E], Bs[E];
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const float2* col = args.div_in + q * args.div_stride + colofs;
+            float2 v[E];
+#pragma unroll
+            for (int i = 0; i < E; ++i) v[i] = act ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
+            fft_column<N, -1, N>(v, p, buf + c, TZ, tw);
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int sx = signed_idx(p + P * i, N);
+                if (q < 3) {
+                    const float kq = kF * (float)(q == 0 ? sx : (q == 1 ? sy : sz));
+                    const float2 t = cmul_i<+1>(cscale(v[i], kq));            // i k_q V_q
+                    A[i] = q == 0 ? t : cadd(A[i], t);
+                } else {
+                    const float k2 = kF * kF * (float)(sx * sx + syz);
+                    Bs[i] = cscale(v[i], -0.5f * k2);                        // -(k^2 / 2) S
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            xd[i] = make_float2(fmaf(args.cdA, A[i].x, args.cdB * Bs[i].x), fmaf(args.cdA, A[i].y, args.cdB * Bs[i].y));
+            xt[i] = make_float2(fmaf(args.ctA, A[i].x, args.ctB * Bs[i].x), fmaf(args.ctA, A[i].y, args.ctB * Bs[i].y));
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            xd[i] = act ? args.src0[colofs + (p + P * i) * estride] : make_float2(0.f, 0.f);
+            xt[i] = (act && two) ? args.src1[colofs + (p + P * i) * estride] : xd[i];
+        }
+        __syncthreads();
+    }
+    if constexpr (MODE >= 1) {
+        if constexpr (MODE == 1) {
+            fft_column<N, -1, N>(xd, p, buf + c, TZ, tw);
+            if (two) fft_column<N, -1, N>(xt, p, buf + c, TZ, tw);
+        }
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int n = p + P * i;
@@ -1193,14 +1231,18 @@ struct Launch {
         const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
         const float kF = (float)g.kF, ikF2 = (float)(1.0 / (g.kF * g.kF));
         cudaError_t e;
-        if (a.fwd_first) {
-            e = set_smem(k_xexp<N, TZC, true>, smem);
+        if (a.fwd_first && a.div_in) {
+            e = set_smem(k_xexp<N, TZC, 2>, smem);
             if (e != cudaSuccess) return e;
-            k_xexp<N, TZC, true><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+            k_xexp<N, TZC, 2><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+        } else if (a.fwd_first) {
+            e = set_smem(k_xexp<N, TZC, 1>, smem);
+            if (e != cudaSuccess) return e;
+            k_xexp<N, TZC, 1><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
         } else {
-            e = set_smem(k_xexp<N, TZC, false>, smem);
+            e = set_smem(k_xexp<N, TZC, 0>, smem);
             if (e != cudaSuccess) return e;
-            k_xexp<N, TZC, false><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+            k_xexp<N, TZC, 0><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
         }
         return cudaGetLastError();
     }
@@ -1345,6 +1387,8 @@ struct Launch {
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zr2c(g, in, out, fs, count, scale, s);           \
     }                                                                                                      \
     cudaError_t transform_xexp_##N(const Geo& g, const XExpArgs& a, int v, cudaStream_t s) {               \
+        if (a.fwd_first && a.div_in) /* four input columns in registers: the narrower tile */              \
+            return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::xexp(g, a, s);                                   \
         return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::xexp(g, a, s)                                    \
                  : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::xexp(g, a, s);                                   \
     }                                                                                                      \

@@ -49,6 +49,16 @@ def test_plan_create_rejects_bad_sizes_before_touching_cuda(lib):
         assert lib.gridspt_last_error()
 
 
+def test_plan_create_rejects_unknown_source_form(lib):
+    from paper_1807_04215_gb300 import _lib
+    for form in (-1, 2, 7):
+        d = _lib.GridsptDesc(64, 3, 1, form, 100.0, 0.0, 0.0)
+        h = ctypes.c_void_p()
+        assert lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1, form
+        assert h.value is None
+        assert b"form" in lib.gridspt_last_error()
+
+
 def test_null_plan_is_rejected(lib):
     b = ctypes.c_size_t()
     assert lib.gridspt_workspace_size(None, ctypes.byref(b)) == 1
