@@ -223,7 +223,8 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
 /* Autotuner for the transform passes (not part of the paper's method). Each
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
  * 4 contiguous-axis forward pass) has two variants for N >= 128 (identical for
- * smaller N). The y expansion has a third, TMA-staged one (N >= 128). The z
+ * smaller N). The y expansion has a third, TMA-staged one (N >= 128), and a
+ * fourth with two adjacent columns per thread (16-byte accesses). The z
  * expansion and the contiguous-axis forward pass have a third that runs one z
  * row per group of warp lanes without block-wide barriers (power-of-two
  * N <= 512; other sizes run variant 0 when it is chosen); the z expansion's
@@ -233,7 +234,7 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
  * bytes, contents overwritten) with CUDA events on `stream`, keeps the fastest
  * in the plan and writes the choices to choices_out (host int32[5], may be
  * NULL). It synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning
- * store and read the choices (0 or 1; 0..2 for passes 2, 3 and 4), e.g.
+ * store and read the choices (0 or 1; 0..3 for pass 2; 0..2 for passes 3 and 4), e.g.
  * from a cache kept by the caller.
  * Results are bitwise identical for all variants: they only change how
  * columns and rows are grouped into thread blocks and warps. */

@@ -279,4 +279,89 @@ __device__ __forceinline__ void fft_row(float2 (&x)[fft_elems(L)], int p, float2
     fft_row_stages<L, 0, DIR>(x, p, row, twl);
 }
 
+
+// ------------------------------------------------------ column-pair variant
+// The same transform for two adjacent columns held by one thread (x[0], x[1]):
+// each butterfly of fft_stage is done for both columns with one twiddle load,
+// and the exchange moves both columns' elements in one 16-byte access (the
+// buffer holds the two columns interleaved, i.e. the float2 layout of
+// fft_column with columns 2c, 2c + 1). Per column the arithmetic is that of
+// fft_stage, so results are bitwise equal.
+template <int L, int S, int DIR, int N>
+__device__ __forceinline__ void fft_stage_pair(float2 (&x)[2][fft_elems(L)], int p, float4* col, int SN,
+                                               const float2* __restrict__ tw) {
+    constexpr int E = fft_elems(L);
+    constexpr int P = L / E;
+    constexpr int R = fft_radix(L, S);
+    constexpr int Ls = fft_ls(L, S);
+    constexpr int Q = E / R;
+    constexpr bool last = (S == fft_nstages(L) - 1);
+    constexpr int TWS = N / (Ls * R);
+    float2 y[2][E];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 v0[R], v1[R];
+        const int b = p + q * P;
+        const int k = (Ls == 1) ? 0 : (b % Ls);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            v0[t] = x[0][q + t * Q];
+            v1[t] = x[1][q + t * Q];
+        }
+        if constexpr (Ls > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w = tw[t * k * TWS];
+                if (DIR < 0) w.y = -w.y;
+                v0[t] = cmul(v0[t], w);
+                v1[t] = cmul(v1[t], w);
+            }
+        }
+        dft_small<R, DIR>(v0);
+        dft_small<R, DIR>(v1);
+        if constexpr (last) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                y[0][q + t * Q] = v0[t];
+                y[1][q + t * Q] = v1[t];
+            }
+        } else {
+            const int base = (b / Ls) * Ls * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) col[(base + t * Ls) * SN] = make_float4(v0[t].x, v0[t].y, v1[t].x, v1[t].y);
+        }
+    }
+    if constexpr (last) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            x[0][i] = y[0][i];
+            x[1][i] = y[1][i];
+        }
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float4 u = col[(p + P * i) * SN];
+            x[0][i] = make_float2(u.x, u.y);
+            x[1][i] = make_float2(u.z, u.w);
+        }
+        __syncthreads();
+    }
+}
+
+template <int L, int S, int DIR, int N>
+__device__ __forceinline__ void fft_stages_pair(float2 (&x)[2][fft_elems(L)], int p, float4* col, int SN,
+                                                const float2* __restrict__ tw) {
+    if constexpr (S < fft_nstages(L)) {
+        fft_stage_pair<L, S, DIR, N>(x, p, col, SN, tw);
+        fft_stages_pair<L, S + 1, DIR, N>(x, p, col, SN, tw);
+    }
+}
+
+template <int L, int DIR, int N>
+__device__ __forceinline__ void fft_column_pair(float2 (&x)[2][fft_elems(L)], int p, float4* col, int SN,
+                                                const float2* __restrict__ tw) {
+    fft_stages_pair<L, 0, DIR, N>(x, p, col, SN, tw);
+}
+
 }  // namespace gridspt

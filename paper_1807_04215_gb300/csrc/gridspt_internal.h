@@ -25,7 +25,7 @@ struct Geo {
 };
 
 // number of tile variants per pass (the autotuner times each)
-constexpr int kTuneVariants[TV_COUNT] = {2, 2, 3, 3, 3};
+constexpr int kTuneVariants[TV_COUNT] = {2, 2, 4, 3, 3};
 
 // Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every
 // derived field is c * kx^a * ky^b * kz^g * src(k) with src in {delta, theta,

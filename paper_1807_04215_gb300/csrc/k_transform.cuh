@@ -391,6 +391,67 @@ k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
     }
 }
 
+// Column-pair form of k_yexp: each thread holds two adjacent kz columns, so
+// global and shared accesses move 16 bytes (both columns) and every twiddle
+// load and index computation serves two columns (fft_column_pair); TZ columns
+// (TZ / 2 pairs) per block. Same outputs bit for bit.
+template <int N, int TZ>
+__global__ void __launch_bounds__(TZ / 2 * Cfg<N>::PC)
+k_yexp2(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+    constexpr int M = N / 2, E = fft_elems(N), P = N / E, TP = TZ / 2;
+    static_assert(TZ % 2 == 0 && M % 2 == 0, "column pairs");
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float4* buf = reinterpret_cast<float4*>(sm + N + (N & 1));
+    const int tid = threadIdx.x, c2 = tid % TP, p = tid / TP;
+    load_table(tw, twg, N);
+    const int kz0 = blockIdx.x * TZ + 2 * c2;
+    const int xr = blockIdx.y;
+    const int B = args.band;
+    const bool act0 = kz0 < M && (B <= 0 || kz0 < B);
+    const bool act1 = kz0 + 1 < M && (B <= 0 || kz0 + 1 < B);
+    constexpr long long estride = (long long)M;
+    const long long colofs = (long long)xr * N * M + kz0;
+    float2 xin[2][E];
+    int cur = -1;
+    __syncthreads();
+    for (int f = 0; f < args.nout; ++f) {
+        const int code = args.codes[f];
+        const int in = code & 255, pb = (code >> 8) & 3, slot = code >> 16;
+        if (in != cur) {
+            const float2* col = args.in + in * args.in_stride + colofs;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int sy = signed_idx(p + P * i, N);
+                const bool live = act0 && (B <= 0 || (sy < B && -sy < B));
+                const float4 v = live ? *reinterpret_cast<const float4*>(col + (p + P * i) * estride)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                xin[0][i] = make_float2(v.x, v.y);
+                xin[1][i] = act1 ? make_float2(v.z, v.w) : make_float2(0.f, 0.f);
+            }
+            cur = in;
+        }
+        float2 y[2][E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float ky = kF * (float)signed_idx(p + P * i, N);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) y[h][i] = pb == 0 ? xin[h][i] : cscale(xin[h][i], pb == 1 ? ky : ky * ky);
+        }
+        fft_column_pair<N, +1, N>(y, p, buf + c2, TP, tw);
+        if (act0) {
+            float2* o = args.out + slot * args.out_stride + colofs;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                if (act1)
+                    *reinterpret_cast<float4*>(o + (p + P * i) * estride) = make_float4(y[0][i].x, y[0][i].y, y[1][i].x, y[1][i].y);
+                else
+                    o[(p + P * i) * estride] = y[0][i];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ z expansion
 // Output f = IFFT_z(c kz^g xy-field[in]) as a real row of N values, via the
 // half-length complex transform of the packed row (Nyquist term zero). The
@@ -619,8 +680,10 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
 // targets) with one z row per P consecutive lanes of a warp (P = M / E <= 32,
 // 32 / P rows per warp) instead of block-wide tiles. Each warp runs its rows
 // through every output field on its own:
-//   * the xy-field input rows (contiguous, 16-byte vector loads) are kept in a
-//     per-warp buffer while consecutive outputs share them;
+//   * the xy-field input rows are kept in a per-warp buffer while consecutive
+//     outputs share them; the next distinct input (that of the next output, or
+//     the first of the warp's next row group) is copied into a second buffer by
+//     16-byte cp.async while the current output is transformed;
 //   * the partner rows of the output are copied into per-warp buffers by
 //     16-byte cp.async before the transform and consumed after it;
 //   * the transform exchanges through a per-warp padded buffer (fft_row);
@@ -642,10 +705,9 @@ struct RowCfg {
     static constexpr int HDR = ((NTW + E) * P + 1) / 2 * 2;   // twiddle tables, 16-byte multiple
     static constexpr int MAXP = kMaxPartners;
     static constexpr int WIN = RW * M;                        // input rows of a warp
-    static constexpr int WSTRIDE = WIN * (1 + MAXP) + RW * XROW;
-    static constexpr size_t smem(int nt) {
-        return sizeof(float2) * (HDR + (size_t)kRowWarps * (nt ? WSTRIDE : WIN + RW * XROW));
-    }
+    // per warp: two input buffers (current, next), MAXP partner buffers, exchange rows
+    __host__ __device__ static constexpr int wstride(int nt) { return WIN * (2 + (nt ? MAXP : 0)) + RW * XROW; }
+    static constexpr size_t smem(int nt) { return sizeof(float2) * (HDR + (size_t)kRowWarps * wstride(nt)); }
 };
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -679,15 +741,17 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane / P, p = lane - r * P;
     zrow_tables<N>(twl, twp, twg);
-    float2* win = sm + C::HDR + warp * (NT ? C::WSTRIDE : WIN + RW * C::XROW);   // [RW][M] input rows
-    float2* wpt = win + WIN;                                                       // [MAXP][RW][M] partners
-    float2* xrow = win + WIN * (NT ? 1 + C::MAXP : 1) + r * C::XROW;                // this row's exchange buffer
+    float2* wbase = sm + C::HDR + warp * C::wstride(NT);
+    float2* wpt = wbase + 2 * WIN;                                                 // [MAXP][RW][M] partners
+    float2* xrow = wbase + WIN * (NT ? 2 + C::MAXP : 2) + r * C::XROW;              // this row's exchange buffer
     const YZExpArgs& z = args.z;
     const long long rows = (long long)N * N;
     const long long groups = rows / RW;
+    const long long gstride = (long long)gridDim.x * kRowWarps;
     const long long fstride2 = args.cells / 2;
-    for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups;
-         grp += (long long)gridDim.x * kRowWarps) {
+    int buf = 0;                 // wbase + buf * WIN holds the current input rows
+    bool have_next = false;      // the other buffer holds (or receives) the next input
+    for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups; grp += gstride) {
         const long long row0 = grp * RW, row = row0 + r;
         float2 accA[NA][E], accB[NA][E];
 #pragma unroll
@@ -698,7 +762,7 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
         for (int f = 0; f < z.nout; ++f) {
             const int code = z.codes[f];
             const int in = code & 255, g = (code >> 8) & 3, cc = (code >> 12) & 3, slot = code >> 16;
-            __syncwarp();                                  // earlier reads of win / wpt are done
+            __syncwarp();                                  // earlier reads of the buffers are done
             int np = 0;
             if constexpr (NT > 0) {
 #pragma unroll
@@ -713,19 +777,36 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                             cp_async16(wpt + np * WIN + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
                     }
                 }
-                cp_async_commit();
             }
             if (in != cur) {
-                const float4* src = reinterpret_cast<const float4*>(z.in + in * z.in_stride + row0 * M);
-                float4 v[WIN / 64];
+                if (have_next) {                           // copied during the previous output
+                    buf ^= 1;
+                } else {                                   // the warp's first input
+                    const float4* src = reinterpret_cast<const float4*>(z.in + in * z.in_stride + row0 * M);
+                    float4 v[WIN / 64];
 #pragma unroll
-                for (int u = 0; u < WIN / 64; ++u) v[u] = __ldg(src + lane + 32 * u);
+                    for (int u = 0; u < WIN / 64; ++u) v[u] = __ldg(src + lane + 32 * u);
 #pragma unroll
-                for (int u = 0; u < WIN / 64; ++u) reinterpret_cast<float4*>(win)[lane + 32 * u] = v[u];
-                __syncwarp();
+                    for (int u = 0; u < WIN / 64; ++u) reinterpret_cast<float4*>(wbase + buf * WIN)[lane + 32 * u] = v[u];
+                    __syncwarp();
+                }
                 cur = in;
+                have_next = false;
             }
-            const float2* colp = win + r * M;
+            {   // next distinct input into the other buffer (last read two outputs ago at the latest)
+                const bool last = f + 1 == z.nout;
+                const int nin = last ? (z.codes[0] & 255) : (z.codes[f + 1] & 255);
+                const long long nrow0 = last ? row0 + gstride * RW : row0;
+                if (last ? nrow0 < rows : nin != in) {
+                    const float2* src = z.in + nin * z.in_stride + nrow0 * M;
+                    float2* dst = wbase + (buf ^ 1) * WIN;
+#pragma unroll
+                    for (int u = 0; u < WIN / 64; ++u) cp_async16(dst + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
+                    have_next = true;
+                }
+            }
+            cp_async_commit();
+            const float2* colp = wbase + buf * WIN + r * M;
             float2 x[E];
 #pragma unroll
             for (int i = 0; i < E; ++i) {
@@ -756,9 +837,9 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
 #pragma unroll
                 for (int i = 0; i < E; ++i) dst[row * M + p + P * i] = x[i];
             }
+            cp_async_wait_all();
+            __syncwarp();                                  // partner and next-input rows of every lane have landed
             if constexpr (NT > 0) {
-                cp_async_wait_all();
-                __syncwarp();                              // partner rows of every lane have landed
                 np = 0;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
@@ -1246,6 +1327,15 @@ struct Launch {
         }
         return cudaGetLastError();
     }
+    static cudaError_t yexp2(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
+        const int B = a.band > 0 && a.band < M ? a.band : 0;
+        dim3 grid(((B ? B : M) + TZC - 1) / TZC, N);
+        const size_t smem = sizeof(float2) * (N + (N & 1) + (size_t)N * TZC);
+        cudaError_t e = set_smem(k_yexp2<N, TZC>, smem);
+        if (e != cudaSuccess) return e;
+        k_yexp2<N, TZC><<<grid, TZC / 2 * PC, smem, s>>>(a, g.tw, (float)g.kF);
+        return cudaGetLastError();
+    }
     static cudaError_t yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, N);
@@ -1394,6 +1484,7 @@ struct Launch {
     }                                                                                                      \
     cudaError_t transform_yexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
         if (v == 2 && N >= 128 && a.band <= 0) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp_tma(g, a, s); \
+        if (v == 3) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp2(g, a, s);                          \
         return v == 1 ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::yexp(g, a, s)                               \
                       : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                              \
     }                                                                                                      \

