@@ -18,6 +18,12 @@ J_b(x) = sum_{k in b} e^{i k.x},
     N_tri(b)     = sum_x J_b(x)^3 / N^3   (closed ordered triangles),
 
 and B_tree = 3 E_b[delta_1, delta_1, delta_2] (three equal permutations).
+
+One-loop bispectrum (Eq. ``bk_1loop``): with the triple-product form
+E_b[a, b, c] = L^6 sum_x I_b[a] I_b[b] I_b[c] / sum_x J_b^3, each term of the
+equation is one E_b over an ordered assignment of fields to (k1, k2, k3):
+B_1-loop = sum of the six orderings of (delta_1, delta_2, delta_3) + E[delta_2,
+delta_2, delta_2] + the three orderings of (delta_1, delta_1, delta_4).
 """
 import math
 
@@ -105,3 +111,67 @@ def bispectrum_brute(a_k, b_k, L, edges):
         if cnt:
             E[i] = L ** 6 * acc.real / cnt
     return E, ntri
+
+
+def bispectrum_triple(a_k, b_k, c_k, L, edges):
+    """E_b[a, b, c] = L^6 sum_x I_b[a] I_b[b] I_b[c] / sum_x J_b^3 per shell, and
+    N_tri (as in ``bispectrum_equilateral``)."""
+    N = a_k.shape[0]
+    k, s2 = mode_k(N, L)
+    idx = bin_index(k, s2, edges)
+    nb = len(edges) - 1
+    E = np.zeros(nb)
+    ntri = np.zeros(nb)
+    for i in range(nb):
+        mask = (idx == i).astype(np.float64)
+        Ia = backward(a_k * mask).real
+        Ib = backward(b_k * mask).real
+        Ic = backward(c_k * mask).real
+        J = backward(mask.astype(np.complex128)).real
+        sj3 = np.sum(J ** 3)
+        ntri[i] = sj3 / float(N) ** 3
+        if ntri[i] > 0.5:
+            E[i] = L ** 6 * np.sum(Ia * Ib * Ic) / sj3
+    return E, ntri
+
+
+def bispectrum_triple_brute(a_k, b_k, c_k, L, edges):
+    """Direct enumeration: L^6 sum_{k1+k2+k3=0} a(k1) b(k2) c(k3) / N_tri over
+    ordered triples in the shell (shells well below N/3 only)."""
+    N = a_k.shape[0]
+    k, s2 = mode_k(N, L)
+    idx = bin_index(k, s2, edges)
+    sx, sy, sz = wave_indices(N)
+    nb = len(edges) - 1
+    E = np.zeros(nb)
+    ntri = np.zeros(nb)
+    for i in range(nb):
+        pts = np.argwhere(idx == i)
+        member = idx == i
+        acc = 0.0 + 0.0j
+        cnt = 0
+        for p1 in pts:
+            for p2 in pts:
+                s3 = [-(sx[tuple(p1)] + sx[tuple(p2)]), -(sy[tuple(p1)] + sy[tuple(p2)]),
+                      -(sz[tuple(p1)] + sz[tuple(p2)])]
+                if max(abs(c) for c in s3) >= N // 2:
+                    continue
+                p3 = tuple(int(c) % N for c in s3)
+                if member[p3]:
+                    acc += a_k[tuple(p1)] * b_k[tuple(p2)] * c_k[p3]
+                    cnt += 1
+        ntri[i] = cnt
+        if cnt:
+            E[i] = L ** 6 * acc.real / cnt
+    return E, ntri
+
+
+def bispectrum_one_loop(d1, d2, d3, d4, L, edges):
+    """Eq. ``bk_1loop`` (D_+ = 1) in equilateral shells: the ten ordered terms."""
+    terms = [(d1, d2, d3), (d1, d3, d2), (d2, d1, d3), (d2, d3, d1), (d3, d1, d2), (d3, d2, d1),
+             (d2, d2, d2), (d1, d1, d4), (d1, d4, d1), (d4, d1, d1)]
+    B = 0.0
+    for a, b, c in terms:
+        E, ntri = bispectrum_triple(a, b, c, L, edges)
+        B = B + E
+    return B, ntri

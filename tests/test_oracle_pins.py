@@ -495,3 +495,40 @@ def test_divergence_form_single_plane_wave_all_orders():
             exp[-m % N, 0, 0] = v
         assert np.abs(dk[n] - exp).max() < 1e-15
         assert np.abs(tk[n] - exp).max() < 1e-15
+
+
+# ------------------------------------------------------- one-loop bispectrum
+def test_triple_shell_estimator_equals_triangle_enumeration():
+    """E[a, b, c] from the FFT shell estimator = the direct sum over closed
+    triangles a(k1) b(k2) c(k3) / N_tri, three different random fields."""
+    N, L = 12, 100.0
+    f = [spt.forward(inputs.random_real((N, N, N), 300 + i)) for i in range(3)]
+    for x in f:
+        x[spt.nyquist_mask(N)] = 0
+    kF = 2 * math.pi / L
+    edges = [kF * 0.5, kF * 1.5, kF * 2.5]
+    E, nt = estimators.bispectrum_triple(*f, L, edges)
+    Eb, ntb = estimators.bispectrum_triple_brute(*f, L, edges)
+    assert np.allclose(nt, ntb, rtol=0, atol=1e-9)
+    assert np.allclose(E, Eb, rtol=1e-10, atol=1e-12 * np.abs(Eb).max())
+    Ea, _ = estimators.bispectrum_equilateral(f[0], f[2], L, edges)     # E[a, a, c]
+    Et, _ = estimators.bispectrum_triple(f[0], f[0], f[2], L, edges)
+    assert np.allclose(Ea, Et, rtol=1e-12)
+
+
+def test_one_loop_bispectrum_equals_enumeration_of_its_definition():
+    """Eq. bk_1loop summed term by term over enumerated closed triangles
+    equals the oracle's shell-estimator form (four different fields)."""
+    N, L = 12, 100.0
+    d = [spt.forward(inputs.random_real((N, N, N), 310 + i)) for i in range(4)]
+    for x in d:
+        x[spt.nyquist_mask(N)] = 0
+    kF = 2 * math.pi / L
+    edges = [kF * 0.5, kF * 1.5, kF * 2.5]
+    B, nt = estimators.bispectrum_one_loop(*d, L, edges)
+    d1, d2, d3, d4 = d
+    Bb = 0.0
+    for a, b, c in [(d1, d2, d3), (d1, d3, d2), (d2, d1, d3), (d2, d3, d1), (d3, d1, d2), (d3, d2, d1),
+                    (d2, d2, d2), (d1, d1, d4), (d1, d4, d1), (d4, d1, d1)]:
+        Bb = Bb + estimators.bispectrum_triple_brute(a, b, c, L, edges)[0]
+    assert np.allclose(B, Bb, rtol=1e-10, atol=1e-12 * np.abs(Bb).max())
