@@ -202,6 +202,18 @@ gridspt_status gridspt_bispectrum(gridspt_plan plan, const void* a_k, const void
                                   double* ntri_out, void* ws, size_t ws_bytes,
                                   gridspt_stream stream);
 
+/* Triple-product form of the shell estimator for three fields:
+ *   e_out[i] = L^6 sum_x I_i[a](x) I_i[b](x) I_i[c](x) / sum_x J_i(x)^3,
+ * arguments, workspace, bounds and the cached sum J^3 as for
+ * gridspt_bispectrum (which equals this call with b = a and c = b, bit for
+ * bit). Each ordered term of the one-loop bispectrum (Eq. bk_1loop) is one
+ * such sum; in equilateral shells B_1-loop = 6 E[d1, d2, d3] + E[d2, d2, d2]
+ * + 3 E[d1, d1, d4]. */
+gridspt_status gridspt_bispectrum_triple(gridspt_plan plan, const void* a_k, const void* b_k,
+                                         const void* c_k, int32_t nbins, const double* edges,
+                                         double* e_out, double* ntri_out, void* ws, size_t ws_bytes,
+                                         gridspt_stream stream);
+
 /* Launch batching (not part of the paper's method): the recursion of one or
  * several plans captured once as a single CUDA graph and replayed with one
  * launch. plans[i] may have different grid sizes, orders and batches; branch i
@@ -223,8 +235,10 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
 /* Autotuner for the transform passes (not part of the paper's method). Each
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
  * 4 contiguous-axis forward pass) has two variants for N >= 128 (identical for
- * smaller N). The y expansion has a third, TMA-staged one (N >= 128), and a
- * fourth with two adjacent columns per thread (16-byte accesses). The z
+ * smaller N). The y expansion has a third, TMA-staged one (N >= 128), a
+ * fourth with two adjacent columns per thread (16-byte accesses) and a fifth
+ * that copies the next input's columns by cp.async during the current
+ * input's transforms. The z
  * expansion and the contiguous-axis forward pass have a third that runs one z
  * row per group of warp lanes without block-wide barriers (power-of-two
  * N <= 512; other sizes run variant 0 when it is chosen); the z expansion's
@@ -234,7 +248,7 @@ gridspt_status gridspt_batch_destroy(gridspt_batch batch);
  * bytes, contents overwritten) with CUDA events on `stream`, keeps the fastest
  * in the plan and writes the choices to choices_out (host int32[5], may be
  * NULL). It synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning
- * store and read the choices (0 or 1; 0..3 for pass 2; 0..2 for passes 3 and 4), e.g.
+ * store and read the choices (0 or 1; 0..4 for pass 2; 0..2 for passes 3 and 4), e.g.
  * from a cache kept by the caller.
  * Results are bitwise identical for all variants: they only change how
  * columns and rows are grouped into thread blocks and warps. */

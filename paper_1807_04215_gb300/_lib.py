@@ -46,6 +46,9 @@ SIGNATURES = {
     "gridspt_bispectrum_workspace_size": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t)]),
     "gridspt_bispectrum": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gridspt_bispectrum_triple": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                            ctypes.POINTER(c_double), c_void_p, c_void_p, c_void_p, c_size_t,
+                                            c_void_p]),
     "gridspt_batch_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_void_p),
                                        ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                        ctypes.POINTER(c_size_t), ctypes.POINTER(c_void_p)]),

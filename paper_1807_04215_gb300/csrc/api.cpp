@@ -1254,17 +1254,71 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan p, int32_t nbins, size_t* bytes) {
     if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
     if (nbins < 1 || nbins > kMaxBins) return fail(GRIDSPT_E_INVALID, "nbins=%d outside [1, %d]", nbins, kMaxBins);
-    *bytes = 3 * align256((size_t)field_floats(p) * sizeof(float)) + align256((size_t)shell_blocks(p->geo) * 2 * sizeof(double));
+    *bytes = 4 * align256((size_t)field_floats(p) * sizeof(float)) + align256((size_t)shell_blocks(p->geo) * 2 * sizeof(double));
     return GRIDSPT_OK;
 }
 
-gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins,
-                                  const double* edges, double* e_out, double* ntri_out, void* ws,
-                                  size_t ws_bytes, gridspt_stream stream) {
-    g_err[0] = 0;
+}  // extern "C"
+
+namespace {
+
+// Shell fields of one bispectrum shell: I_a, I_b (, I_c) and, without a cached
+// sum J^3, J, transformed along x (pruned to |ky|, kz < band) and y into
+// out[f] (stride fstride); the z pass follows fused with the sums.
+gridspt_status shell_fields(const gridspt_plan_s* p, const float2* a, const float2* b, const float2* c, bool has_j,
+                            long long lo, long long hi, int band, float2* out, long long fstride, cudaStream_t s) {
+    const double fb = 4.0 * (double)field_floats(p);
+    const double N = p->geo.N, M = p->geo.M;
+    const double fx = band > 0 ? (2.0 * band - 1.0) * band / (N * M) : 1.0;   // x columns
+    const double fy_in = band > 0 ? (2.0 * band - 1.0) / N * band / M : 1.0;   // y inputs
+    const double fy_out = band > 0 ? band / M : 1.0;                         // y outputs
+    auto xpass = [&](const float2* s0, const float2* s1, int first, int count, const int* srcs) -> gridspt_status {
+        XExpArgs xa{};
+        xa.src0 = const_cast<float2*>(s0);
+        xa.src1 = const_cast<float2*>(s1);
+        xa.out = out + first * fstride;
+        xa.out_stride = fstride;
+        xa.s2_nl = -1;
+        xa.shell_lo = lo;
+        xa.shell_hi = hi;
+        xa.band = band;
+        xa.nout = count;
+        for (int f = 0; f < count; ++f) xa.codes[f] = x_code(XK_SHELL, 0, srcs[f]);
+        CKP(PK_BX, fb * fx * ((s0 == s1 ? 1 : 2) + count), s, launch_xexp(p->geo, xa, s), "x pass");
+        return GRIDSPT_OK;
+    };
+    int nf = 0;
+    if (!c) {
+        const int srcs[3] = {XS_DELTA, b == a ? XS_DELTA : XS_THETA, XS_ONE};
+        if (gridspt_status st = xpass(a, b, 0, has_j ? 3 : 2, srcs)) return st;
+        nf = has_j ? 3 : 2;
+    } else {
+        const int s_ab[2] = {XS_DELTA, b == a ? XS_DELTA : XS_THETA};
+        const int s_cj[2] = {XS_DELTA, XS_ONE};
+        if (gridspt_status st = xpass(a, b, 0, 2, s_ab)) return st;
+        if (gridspt_status st = xpass(c, c, 2, has_j ? 2 : 1, s_cj)) return st;
+        nf = has_j ? 4 : 3;
+    }
+    YZExpArgs ya{};
+    ya.in = out;
+    ya.in_stride = fstride;
+    ya.out = out;
+    ya.out_stride = fstride;
+    ya.nout = nf;
+    ya.band = band;
+    for (int f = 0; f < nf; ++f) ya.codes[f] = y_code(f, 0, f);
+    CKP(PK_BY, fb * nf * (fy_in + fy_out), s, launch_yexp(p->geo, ya, s), "y pass");
+    return GRIDSPT_OK;
+}
+
+// E = L^6 sum I_a^2 I_b / sum J^3 (c == NULL) or L^6 sum I_a I_b I_c / sum J^3.
+gridspt_status bispectrum_impl(gridspt_plan p, const void* a_k, const void* b_k, const void* c_k, int32_t nbins,
+                               const double* edges, double* e_out, double* ntri_out, void* ws, size_t ws_bytes,
+                               gridspt_stream stream) {
     if (check_plan(p)) return GRIDSPT_E_INVALID;
     if (!a_k || !b_k || !e_out || !ntri_out) return fail(GRIDSPT_E_INVALID, "NULL argument");
-    if (!aligned16(a_k) || !aligned16(b_k) || !aligned16(ws)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    if (!aligned16(a_k) || !aligned16(b_k) || (c_k && !aligned16(c_k)) || !aligned16(ws))
+        return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
     BinSpec bs{};
     if (gridspt_status st = make_bins(p, nbins, edges, 0, &bs)) return st;
     const long long maxs2 = (long long)bs.thr[nbins] - 1;
@@ -1279,14 +1333,15 @@ gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b
     const size_t fb = align256((size_t)field_floats(p) * sizeof(float));
     char* base = static_cast<char*>(ws);
     float2* fields = reinterpret_cast<float2*>(base);
-    double* partial = reinterpret_cast<double*>(base + 3 * fb);
+    double* partial = reinterpret_cast<double*>(base + 4 * fb);
     const double L = p->d.box;
     const long long fstride = (long long)(fb / sizeof(float2));
     const int G = shell_blocks(p->geo);
     // sum J^3 per shell is data independent: reuse it when the shells match the cached ones
     bool cached = p->j3_nb == nbins;
     for (int i = 0; cached && i <= nbins; ++i) cached = p->j3_thr[i] == bs.thr[i];
-    const int nf = cached ? 2 : 3;
+    const int triple = c_k ? 1 : 0;
+    const int nf = 2 + triple + (cached ? 0 : 1);
     for (int i = 0; i < nbins; ++i) {
         if (bs.thr[i + 1] <= 1) {   // shell holds no mode with k > 0
             CK(cudaMemsetAsync(e_out + i, 0, sizeof(double), s), "bispectrum empty shell");
@@ -1296,14 +1351,16 @@ gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b
         }
         // every mode of the shell has |s_a| < band in each component
         const int band = (int)std::floor(std::sqrt((double)(bs.thr[i + 1] - 1))) + 1;
-        if (gridspt_status st = backward_fields(p, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k),
-                                                fields, fstride, nf, true, bs.thr[i], bs.thr[i + 1], band, true, s))
+        if (gridspt_status st = shell_fields(p, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k),
+                                             static_cast<const float2*>(c_k), !cached, bs.thr[i], bs.thr[i + 1], band,
+                                             fields, fstride, s))
             return st;
         const double fbytes = 4.0 * (double)field_floats(p);
         CKP(PK_BZ, fbytes * nf * ((double)band / p->geo.M), s,
-            launch_zshell(p->geo, fields, fstride, band, nf, partial, s), "bispectrum z pass and sums");
+            launch_zshell(p->geo, fields, fstride, band, nf, triple, partial, s), "bispectrum z pass and sums");
         CKP(PK_BISPEC, 16.0 * G, s,
-            launch_bispec_final(p->geo, partial, G, nf, p->j3 + i, e_out + i, ntri_out + i, L * L * L * L * L * L, s),
+            launch_bispec_final(p->geo, partial, G, cached ? 2 : 3, p->j3 + i, e_out + i, ntri_out + i,
+                                L * L * L * L * L * L, s),
             "bispectrum final sum");
     }
     if (!cached) {
@@ -1311,6 +1368,25 @@ gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b
         for (int i = 0; i <= nbins; ++i) p->j3_thr[i] = bs.thr[i];
     }
     return GRIDSPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gridspt_status gridspt_bispectrum(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins,
+                                  const double* edges, double* e_out, double* ntri_out, void* ws,
+                                  size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    return bispectrum_impl(p, a_k, b_k, nullptr, nbins, edges, e_out, ntri_out, ws, ws_bytes, stream);
+}
+
+gridspt_status gridspt_bispectrum_triple(gridspt_plan p, const void* a_k, const void* b_k, const void* c_k,
+                                         int32_t nbins, const double* edges, double* e_out, double* ntri_out,
+                                         void* ws, size_t ws_bytes, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (!c_k) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    return bispectrum_impl(p, a_k, b_k, c_k, nbins, edges, e_out, ntri_out, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -25,7 +25,7 @@ struct Geo {
 };
 
 // number of tile variants per pass (the autotuner times each)
-constexpr int kTuneVariants[TV_COUNT] = {2, 2, 4, 3, 3};
+constexpr int kTuneVariants[TV_COUNT] = {2, 2, 5, 3, 3};
 
 // Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every
 // derived field is c * kx^a * ky^b * kz^g * src(k) with src in {delta, theta,
@@ -170,13 +170,14 @@ int power_blocks(const Geo& g);
 cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const BinSpec& bins,
                          double* partial, double* p_out, int64_t* nk_out, double volume,
                          cudaStream_t s);
-// Bispectrum, one shell: z transform of the xy-fields I_a, I_b (and J when
-// nfields = 3; kz < band) fused with the sums of I_a^2 I_b (and J^3), per-block
-// partials, then the fixed-order final reduction. sum J^3 does not depend on
-// the data: with nfields = 3 the final kernel stores it in *j3_cache, with 2
-// it reads it from there.
+// Bispectrum, one shell: z transform of the xy-fields I_a, I_b (and I_c when
+// triple; then J when present; kz < band) fused with the sums of I_a^2 I_b or
+// I_a I_b I_c (and J^3), per-block partials, then the fixed-order final
+// reduction. nfields counts the data fields and J. sum J^3 does not depend on
+// the data: with has_j (nfields 3 in the final kernel's convention) the final
+// kernel stores it in *j3_cache, otherwise it reads it from there.
 int shell_blocks(const Geo& g);
-cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, int nfields,
+cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, int nfields, int triple,
                           double* partial, cudaStream_t s);
 cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, int nfields, double* j3_cache,
                                 double* e_out, double* ntri_out, double vol2, cudaStream_t s);

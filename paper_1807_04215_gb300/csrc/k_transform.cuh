@@ -345,13 +345,18 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
 // input are consecutive; the input column is loaded once and kept in
 // registers. In-place use (out == in, one output per input, same index) is
 // safe: a block owns its columns.
-template <int N, int TZ>
+//
+// PF: the next input's column tile is copied into a second shared buffer by
+// cp.async (8-byte, zero-filled where the band excludes it) while the outputs
+// of the current input are transformed.
+template <int N, int TZ, bool PF>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PC)
 k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* buf = sm + N;
+    float2* pre = buf + N * TZ;                  // PF: next input tile, element (n, c) at n * TZ + c
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
     const int kz = blockIdx.x * TZ + c;
@@ -362,19 +367,44 @@ k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
     const long long colofs = (long long)xr * N * M + kz;
     float2 xin[E];
     int cur = -1;
+    bool have_next = false;
     __syncthreads();
     for (int f = 0; f < args.nout; ++f) {
         const int code = args.codes[f];
         const int in = code & 255, pb = (code >> 8) & 3, slot = code >> 16;
         if (in != cur) {
-            const float2* col = args.in + in * args.in_stride + colofs;
+            if (PF && have_next) {
+                cp_async_wait_all();
+                __syncthreads();                 // every thread's copies have landed
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                const int sy = signed_idx(p + P * i, N);
-                const bool live = act && (B <= 0 || (sy < B && -sy < B));
-                xin[i] = live ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
+                for (int i = 0; i < E; ++i) xin[i] = pre[(p + P * i) * TZ + c];
+            } else {
+                const float2* col = args.in + in * args.in_stride + colofs;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int sy = signed_idx(p + P * i, N);
+                    const bool live = act && (B <= 0 || (sy < B && -sy < B));
+                    xin[i] = live ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
+                }
             }
             cur = in;
+            have_next = false;
+            if constexpr (PF) {                  // the next distinct input, if any
+                int g2 = f + 1;
+                while (g2 < args.nout && (args.codes[g2] & 255) == in) ++g2;
+                if (g2 < args.nout) {
+                    __syncthreads();             // everyone has read the previous prefetch
+                    const float2* col = args.in + (args.codes[g2] & 255) * args.in_stride + colofs;
+#pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        const int sy = signed_idx(p + P * i, N);
+                        const bool live = act && (B <= 0 || (sy < B && -sy < B));
+                        cp_async8(pre + (p + P * i) * TZ + c, live ? col + (p + P * i) * estride : col, live ? 8 : 0);
+                    }
+                    cp_async_commit();
+                    have_next = true;
+                }
+            }
         }
         float2 y[E];
 #pragma unroll
@@ -1024,13 +1054,17 @@ __device__ __forceinline__ void kahan_add2(float& s, float& c, float x) {
     c = (t - s) - y;
     s = t;
 }
-// a^2 b summed over the two cells of a float2, with explicit roundings (no
-// contraction), so that every shell kernel forms bitwise the same terms
-__device__ __forceinline__ float cell_sq_mul(float2 a, float2 b) {
-    return __fadd_rn(__fmul_rn(__fmul_rn(a.x, a.x), b.x), __fmul_rn(__fmul_rn(a.y, a.y), b.y));
+// a b c summed over the two cells of a float2, with explicit roundings (no
+// contraction), so that every shell kernel forms bitwise the same terms (and
+// a a b here is bitwise the a^2 b of the two-field estimator)
+__device__ __forceinline__ float cell_mul3(float2 a, float2 b, float2 c) {
+    return __fadd_rn(__fmul_rn(__fmul_rn(a.x, b.x), c.x), __fmul_rn(__fmul_rn(a.y, b.y), c.y));
 }
 
-template <int N, int TZ, int NF>
+// TRI: the data fields are I_a, I_b, I_c and the first sum is I_a I_b I_c
+// (triple-product estimator, one-loop bispectrum); otherwise I_a, I_b and
+// I_a^2 I_b. NF counts the data fields plus J when present.
+template <int N, int TZ, int NF, bool TRI>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
 k_zshell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
          double* __restrict__ partial) {
@@ -1078,12 +1112,13 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < NF; ++f) fft_column<M, +1, N>(x[f], p, t3 + f * TZ * PITCH + c * PITCH, 1, tw);
+    constexpr int ND = TRI ? 3 : 2;                   // data fields; J follows when NF > ND
     float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
     if (row0 + c < rows) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            kahan_add2(s1, c1, cell_sq_mul(x[0][i], x[1][i]));            // cells 2n, 2n + 1
-            if constexpr (NF == 3) kahan_add2(s2, c2, cell_sq_mul(x[NF - 1][i], x[NF - 1][i]));
+            kahan_add2(s1, c1, cell_mul3(x[0][i], TRI ? x[1][i] : x[0][i], x[TRI ? 2 : 1][i]));   // cells 2n, 2n + 1
+            if constexpr (NF > ND) kahan_add2(s2, c2, cell_mul3(x[NF - 1][i], x[NF - 1][i], x[NF - 1][i]));
         }
     }
     const double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
@@ -1130,7 +1165,7 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
 // a shuffle tree over the row's P lanes, rows added in order, one FP64
 // partial pair per group. Terms, tree and order are those of the tile kernel,
 // so the partials are bitwise equal.
-template <int N, int NF>
+template <int N, int NF, bool TRI>
 __global__ void __launch_bounds__(kRowWarps * 32, 2)
 k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
              double* __restrict__ partial) {
@@ -1152,9 +1187,8 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
         double acc1 = 0.0, acc2 = 0.0;
         for (int rr = 0; rr < G; rr += RW) {
             const long long row = grp * G + rr + r;
-            float2 x[NF][E];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
+            // one band-limited row of field f, packed and transformed to real cells
+            auto real_row = [&](int f, float2 (&x)[E]) {
                 const float2* src = in + f * in_stride + row * M;
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
@@ -1164,16 +1198,24 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
                                         : make_float2(0.f, 0.f);
                     const float2 Ev = cadd(Xk, Xm);
                     const float2 Ov = cmul(csub(Xk, Xm), twp[i * P + p]);
-                    x[f][i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
+                    x[i] = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
                 }
-            }
-#pragma unroll
-            for (int f = 0; f < NF; ++f) fft_row<M, +1>(x[f], p, xrow, twl);
+                fft_row<M, +1>(x, p, xrow, twl);
+            };
+            constexpr int ND = TRI ? 3 : 2;               // data fields; J follows when NF > ND
             float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+            {
+                float2 x[ND][E];
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                kahan_add2(s1, c1, cell_sq_mul(x[0][i], x[1][i]));
-                if constexpr (NF == 3) kahan_add2(s2, c2, cell_sq_mul(x[NF - 1][i], x[NF - 1][i]));
+                for (int f = 0; f < ND; ++f) real_row(f, x[f]);
+#pragma unroll
+                for (int i = 0; i < E; ++i) kahan_add2(s1, c1, cell_mul3(x[0][i], x[TRI ? 1 : 0][i], x[ND - 1][i]));
+            }
+            if constexpr (NF > ND) {                      // J after the data fields: fewer live registers
+                float2 xj[E];
+                real_row(NF - 1, xj);
+#pragma unroll
+                for (int i = 0; i < E; ++i) kahan_add2(s2, c2, cell_mul3(xj[i], xj[i], xj[i]));
             }
             double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
 #pragma unroll
@@ -1336,13 +1378,14 @@ struct Launch {
         k_yexp2<N, TZC><<<grid, TZC / 2 * PC, smem, s>>>(a, g.tw, (float)g.kF);
         return cudaGetLastError();
     }
+    template <bool PF = false>
     static cudaError_t yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, N);
-        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
-        cudaError_t e = set_smem(k_yexp<N, TZC>, smem);
+        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PF ? 2 : 1));
+        cudaError_t e = set_smem(k_yexp<N, TZC, PF>, smem);
         if (e != cudaSuccess) return e;
-        k_yexp<N, TZC><<<grid, TZC * PC, smem, s>>>(a, g.tw, (float)g.kF);
+        k_yexp<N, TZC, PF><<<grid, TZC * PC, smem, s>>>(a, g.tw, (float)g.kF);
         return cudaGetLastError();
     }
     template <bool PF>
@@ -1420,7 +1463,7 @@ struct Launch {
         }
     }
     static int shell_blocks() { return (int)(((long long)N * N + TZZ - 1) / TZZ); }
-    template <int NF>
+    template <int NF, bool TRI>
     static cudaError_t zrow_shell(const Geo& g, const float2* in, long long st, int band, double* partial,
                                   cudaStream_t s) {
         using C = RowCfg<N>;
@@ -1428,36 +1471,44 @@ struct Launch {
             return cudaErrorNotSupported;
         } else {
             const size_t smem = sizeof(float2) * (C::HDR + (size_t)kRowWarps * C::RW * C::XROW);
-            cudaError_t e = set_smem(k_zrow_shell<N, NF>, smem);
+            cudaError_t e = set_smem(k_zrow_shell<N, NF, TRI>, smem);
             if (e != cudaSuccess) return e;
             int dev = 0, sms = 0, per = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow_shell<N, NF>, kRowWarps * 32,
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow_shell<N, NF, TRI>, kRowWarps * 32,
                                                                      smem)) != cudaSuccess)
                 return e;
             const long long groups = (long long)N * N / Cfg<N>::TZZ0;
             const long long need = (groups + kRowWarps - 1) / kRowWarps;
             const long long resident = (long long)(per > 0 ? per : 1) * sms;
-            k_zrow_shell<N, NF><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
+            k_zrow_shell<N, NF, TRI><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
                 in, st, band, g.tw, partial);
             return cudaGetLastError();
         }
     }
-    static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, double* partial,
-                              cudaStream_t s) {
-        if (g.var[TV_ZEXP] == 2 && RowCfg<N>::ok && TZZ == Cfg<N>::TZZ0)
-            return nf == 3 ? zrow_shell<3>(g, in, st, band, partial, s) : zrow_shell<2>(g, in, st, band, partial, s);
-        const size_t smem = sizeof(float2) * (N + (size_t)nf * TZZ * PITCH);
-        cudaError_t e;
-        if (nf == 3) {
-            if ((e = set_smem(k_zshell<N, TZZ, 3>, smem)) != cudaSuccess) return e;
-            k_zshell<N, TZZ, 3><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
-        } else {
-            if ((e = set_smem(k_zshell<N, TZZ, 2>, smem)) != cudaSuccess) return e;
-            k_zshell<N, TZZ, 2><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
-        }
+    template <int NF, bool TRI>
+    static cudaError_t zshell_tile(const Geo& g, const float2* in, long long st, int band, double* partial,
+                                   cudaStream_t s) {
+        const size_t smem = sizeof(float2) * (N + (size_t)NF * TZZ * PITCH);
+        cudaError_t e = set_smem(k_zshell<N, TZZ, NF, TRI>, smem);
+        if (e != cudaSuccess) return e;
+        k_zshell<N, TZZ, NF, TRI><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
         return cudaGetLastError();
+    }
+    // nf: data fields (2: a, b; 3 with tri: a, b, c) plus J when present
+    static cudaError_t zshell(const Geo& g, const float2* in, long long st, int band, int nf, int tri,
+                              double* partial, cudaStream_t s) {
+        if (g.var[TV_ZEXP] == 2 && RowCfg<N>::ok && TZZ == Cfg<N>::TZZ0) {
+            if (tri) return nf == 4 ? zrow_shell<4, true>(g, in, st, band, partial, s)
+                                    : zrow_shell<3, true>(g, in, st, band, partial, s);
+            return nf == 3 ? zrow_shell<3, false>(g, in, st, band, partial, s)
+                           : zrow_shell<2, false>(g, in, st, band, partial, s);
+        }
+        if (tri) return nf == 4 ? zshell_tile<4, true>(g, in, st, band, partial, s)
+                                : zshell_tile<3, true>(g, in, st, band, partial, s);
+        return nf == 3 ? zshell_tile<3, false>(g, in, st, band, partial, s)
+                       : zshell_tile<2, false>(g, in, st, band, partial, s);
     }
 };
 
@@ -1485,8 +1536,9 @@ struct Launch {
     cudaError_t transform_yexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
         if (v == 2 && N >= 128 && a.band <= 0) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp_tma(g, a, s); \
         if (v == 3) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp2(g, a, s);                          \
-        return v == 1 ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::yexp(g, a, s)                               \
-                      : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp(g, a, s);                              \
+        if (v == 4) return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<true>(g, a, s);             \
+        return v == 1 ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<false>(g, a, s)               \
+                      : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template yexp<false>(g, a, s);              \
     }                                                                                                      \
     cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
         if (v == 2 && RowCfg<N>::ok) {                                                                    \
@@ -1505,8 +1557,8 @@ struct Launch {
         return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZP>::zexp_pairs(g, a, s);                                 \
     }                                                                                                      \
     cudaError_t transform_zshell_##N(const Geo& g, const float2* in, long long st, int band, int nf,       \
-                                     double* partial, cudaStream_t s) {                                    \
-        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zshell(g, in, st, band, nf, partial, s);             \
+                                     int tri, double* partial, cudaStream_t s) {                           \
+        return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zshell(g, in, st, band, nf, tri, partial, s);        \
     }
 
 }  // namespace gridspt

@@ -17,7 +17,7 @@ namespace gridspt {
     cudaError_t transform_zexp_##N(const Geo&, const YZExpArgs&, int, cudaStream_t);                       \
     int transform_shell_blocks_##N();                                                                      \
     cudaError_t transform_zexp_pairs_##N(const Geo&, const ZPairArgs&, cudaStream_t);                      \
-    cudaError_t transform_zshell_##N(const Geo&, const float2*, long long, int, int, double*, cudaStream_t);
+    cudaError_t transform_zshell_##N(const Geo&, const float2*, long long, int, int, int, double*, cudaStream_t);
 GRIDSPT_ALL_N(GRIDSPT_DECLARE)
 #undef GRIDSPT_DECLARE
 
@@ -97,10 +97,10 @@ int shell_blocks(const Geo& g) {
     }
 }
 
-cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, int nfields, double* partial,
-                          cudaStream_t s) {
+cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, int band, int nfields, int triple,
+                          double* partial, cudaStream_t s) {
     switch (g.N) {
-#define GRIDSPT_CASE(n) case n: return transform_zshell_##n(g, in, in_stride, band, nfields, partial, s);
+#define GRIDSPT_CASE(n) case n: return transform_zshell_##n(g, in, in_stride, band, nfields, triple, partial, s);
         GRIDSPT_ALL_N(GRIDSPT_CASE)
 #undef GRIDSPT_CASE
         default: return cudaErrorInvalidValue;

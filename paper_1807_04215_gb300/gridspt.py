@@ -279,6 +279,36 @@ def bispectrum(plan, a, b, edges, ws=None):
     return E, nt
 
 
+def bispectrum_triple(plan, a, b, c, edges, ws=None):
+    """Equilateral shell triple product E = L^6 sum I_a I_b I_c / sum J^3 and N_tri
+    per shell (gridspt_bispectrum_triple)."""
+    for t, name in ((a, "a"), (b, "b"), (c, "c")):
+        plan._check_half(t, (), name)
+    e, nb = _edges(edges)
+    E = torch.empty(nb, dtype=torch.float64, device="cuda")
+    nt = torch.empty(nb, dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = torch.empty(bispectrum_workspace_size(plan, nb), dtype=torch.uint8, device="cuda")
+    _lib.check("gridspt_bispectrum_triple",
+               plan.lib.gridspt_bispectrum_triple(plan.handle, _ptr(a), _ptr(b), _ptr(c), nb, e, _ptr(E), _ptr(nt),
+                                                  _ptr(ws), ws.numel(), _stream()))
+    return E, nt
+
+
+def bispectrum_one_loop(plan, d1, d2, d3, d4, edges, ws=None):
+    """One-loop bispectrum of Eq. bk_1loop (D_+ = 1) in equilateral shells:
+    B = 6 E[d1, d2, d3] + E[d2, d2, d2] + 3 E[d1, d1, d4] (the ten ordered terms
+    of the equation collapse to these three sums when all |k_i| share a shell).
+    Returns (B, N_tri)."""
+    e, nb = _edges(edges)
+    if ws is None:
+        ws = torch.empty(bispectrum_workspace_size(plan, nb), dtype=torch.uint8, device="cuda")
+    e123, nt = bispectrum_triple(plan, d1, d2, d3, edges, ws)
+    e222, _ = bispectrum_triple(plan, d2, d2, d2, edges, ws)
+    e114, _ = bispectrum_triple(plan, d1, d1, d4, edges, ws)
+    return 6.0 * e123 + e222 + 3.0 * e114, nt
+
+
 def default_kcut(n, n_max, box):
     """2 k_Ny / (n_max + 1) in h/Mpc."""
     return 2.0 * math.pi / box * n / (n_max + 1)

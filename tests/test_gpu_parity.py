@@ -366,6 +366,53 @@ def test_bispectrum_matches_oracle(N, L, nb):
     assert np.all(np.abs(E[sel] - Er[sel]) <= 1e-4 * np.abs(Er[sel]).max())
 
 
+@pytest.mark.parametrize("N,L,nb", [(32, 250.0, 5), (48, 300.0, 6)])
+def test_triple_and_one_loop_bispectrum_match_oracle(N, L, nb):
+    """E[a, b, c] for three different fields and the one-loop bispectrum of
+    Eq. bk_1loop (GPU: 6 E[1,2,3] + E[2,2,2] + 3 E[1,1,4]; oracle: the ten
+    ordered terms) on the oracle's fields rounded to FP32; E within 1e-4 of
+    its scale, N_tri within FP32 rounding of the cubes."""
+    n_max = 4
+    plan = g.Plan(N, n_max, L)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, 29)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    dk, _ = spt.run_orders(ref1, L, n_max)
+    r = [ref1] + [inputs.half_to_full(inputs.full_to_half(dk[n]).astype(np.complex64)) for n in (2, 3, 4)]
+    dev = [to_dev(x) for x in r]
+    kc = 2 * math.pi / L * N / (n_max + 1)
+    edges = [kc * i / nb for i in range(nb + 1)]
+    E, nt = g.bispectrum_triple(plan, dev[0], dev[1], dev[2], edges)
+    Er, ntr = estimators.bispectrum_triple(r[0], r[1], r[2], L, edges)
+    assert np.allclose(nt.cpu().numpy(), ntr, rtol=1e-6, atol=1e-3)
+    sel = ntr > 0.5
+    E = E.cpu().numpy()
+    assert np.all(np.abs(E[sel] - Er[sel]) <= 1e-4 * np.abs(Er[sel]).max())
+    B, _ = g.bispectrum_one_loop(plan, *dev, edges)
+    Br, _ = estimators.bispectrum_one_loop(*r, L, edges)
+    B = B.cpu().numpy()
+    assert np.all(np.abs(B[sel] - Br[sel]) <= 1e-4 * np.abs(Br[sel]).max())
+
+
+def test_triple_estimator_with_repeated_field_is_the_two_field_estimator():
+    """E[a, a, b] of the triple form equals E[a, b] of gridspt_bispectrum bit for
+    bit (same terms a a b, same sums, same sum J^3), in every z-pass variant."""
+    N, L, nb = 64, 400.0, 6
+    kc = 2 * math.pi / L * N / 4
+    edges = [kc * i / nb for i in range(nb + 1)]
+    outs = []
+    for choice in ([0] * 5, [0, 0, 0, 2, 0]):
+        p1, p2 = g.Plan(N, 3, L), g.Plan(N, 3, L)
+        for pl in (p1, p2):
+            g.set_tuning(pl, choice)
+        d1 = g.make_linear_field(p1, [8])
+        sp = g.run_orders(p1, d1)
+        two = g.bispectrum(p1, d1[0], sp[0, 0, 0], edges)
+        tri = g.bispectrum_triple(p2, d1[0], d1[0], sp[0, 0, 0], edges)
+        assert torch.equal(two[0], tri[0]) and torch.equal(two[1], tri[1])
+        outs.append([t.clone() for t in g.bispectrum_triple(p2, d1[0], sp[0, 0, 0], sp[0, 1, 0], edges)])
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
 def test_bispectrum_reuses_shell_normalisation_across_calls():
     """The first call stores sum J^3 per shell in the plan; repeated calls with
     the same shells reuse it and agree bit for bit; new shells recompute."""
