@@ -125,7 +125,11 @@ gridspt_status gridspt_make_linear_field(gridspt_plan plan, const gridspt_cosmo*
                                          gridspt_stream stream);
 
 /* Sec. II.C steps (2)-(6) repeated to order n_max (Eq. recursion_formula):
- *   delta1_k: device float2[batch][N][N][N/2] (read only).
+ *   delta1_k: device float2[batch][N][N][N/2] (read only). Its modes with
+ *             |s|^2 > (kcut_lin / k_F)^2 (default cut 2 k_Ny / (n_max + 1))
+ *             are taken as zero, the cut of Sec. II.C on the linear field, as
+ *             gridspt_make_linear_field writes them; the order-1 passes move
+ *             only the columns inside that cut.
  *   spectra:  device float2[batch][n_max-1][2][N][N][N/2]; slot [b][n-2][0] is
  *             delta_n(k), [b][n-2][1] is theta_n(k), n = 2..n_max (written for
  *             n >= start_order, read for 2 <= n < start_order).

@@ -481,7 +481,8 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
         a.cells = cells;
         a.store = (store && first == 0) ? ws + (long long)order_base(m) * cells : nullptr;
         a.ntargets = 0;
-        double bytes = fb * za.nout * (a.store ? 1 : 0) + fb * (m == 1 ? 9 : 12);   // stores + xy-field inputs
+        const double fz = za.band > 0 ? (double)za.band / p->geo.M : 1.0;             // band-limited inputs
+        double bytes = fb * za.nout * (a.store ? 1 : 0) + fb * fz * (m == 1 ? 9 : 12);   // stores + xy-field inputs
         // a launch holds at most kMaxPairTargets targets and kMaxPartners partner
         // fields per output over all its targets (order 1 supplies at most one
         // partner per output, higher orders two)
@@ -532,6 +533,24 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
     return GRIDSPT_OK;
 }
 
+// Order 1 from delta_1, whose modes above the linear cut (|s|^2 > s2_lin, Sec.
+// II.C step (1)) are zero: the x pass applies that cut to its input and moves
+// only the columns with |ky|, kz < band; the y pass forms only kz < band
+// columns; the z pass reads only kz < band. band = floor(sqrt(s2_lin)) + 1
+// bounds every component of an in-band wavevector. The skipped columns hold
+// zeros in the full computation, so the fields are the same.
+void order1_band(const gridspt_plan_s* p, XExpArgs& xa, YZExpArgs& ya, YZExpArgs& za, double* fx, double* fy_in,
+                 double* fy_out) {
+    xa.s2_in = p->s2_lin;
+    const int band = (int)std::floor(std::sqrt((double)p->s2_lin)) + 1;
+    if (band >= p->geo.M) return;
+    const double N = p->geo.N, M = p->geo.M;
+    xa.band = ya.band = za.band = band;
+    *fx = (2.0 * band - 1.0) * band / (N * M);
+    *fy_in = (2.0 * band - 1.0) / N * band / M;
+    *fy_out = band / M;
+}
+
 // Derived fields of order m from its spectra (Sec. II.C steps (2)/(5)),
 // written to ws at the order's slot, through the factorised x, y and z
 // expansion passes. With fwd, the spectra buffers hold the y-transformed
@@ -573,10 +592,13 @@ gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* 
     za.out = nullptr;
     za.out_stride = F;
     expansion_codes(m, xa, ya, za);
+    xa.s2_in = -1;
     const int nin = m == 1 ? 1 : 2;
-    CKP(fwd ? PK_XEXP_FWD : PK_XEXP, fb * (fwd ? 2 * nin + xa.nout : nin + xa.nout), s,
+    double fx = 1.0, fy_in = 1.0, fy_out = 1.0;
+    if (m == 1) order1_band(p, xa, ya, za, &fx, &fy_in, &fy_out);
+    CKP(fwd ? PK_XEXP_FWD : PK_XEXP, fb * fx * (fwd ? 2 * nin + xa.nout : nin + xa.nout), s,
         launch_xexp(p->geo, xa, s), "x expansion");
-    CKP(PK_YEXP, fb * (xa.nout + ya.nout), s, launch_yexp(p->geo, ya, s), "y expansion");
+    CKP(PK_YEXP, fb * (fy_in * xa.nout + fy_out * ya.nout), s, launch_yexp(p->geo, ya, s), "y expansion");
     return zexp_pairs(p, m, za, ws, start, spec_delta, s);
 }
 
@@ -662,11 +684,14 @@ gridspt_status derive_order_div(const gridspt_plan_s* p, int m, float2* dk, floa
         xa.codes[1] = x_code(XK_POW, 0, XS_PHI);
         xa.codes[2] = x_code(XK_POW, 1, XS_PHI);
     }
+    xa.s2_in = -1;
+    YZExpArgs ya{}, za{};
+    double fx = 1.0, fy_in = 1.0, fy_out = 1.0;
+    if (m == 1) order1_band(p, xa, ya, za, &fx, &fy_in, &fy_out);
     const int nin = src ? 4 : (m == 1 ? 1 : 2);
-    CKP(src ? (m < n_max ? PK_XEXP_FWD : PK_X_FWD) : PK_XEXP, fb * (nin + (src ? 2 : 0) + xa.nout), s,
+    CKP(src ? (m < n_max ? PK_XEXP_FWD : PK_X_FWD) : PK_XEXP, fb * fx * (nin + (src ? 2 : 0) + xa.nout), s,
         launch_xexp(p->geo, xa, s), "x pass (divergence form)");
     if (m == n_max) return GRIDSPT_OK;
-    YZExpArgs ya{}, za{};
     ya.in = xs;
     ya.in_stride = F;
     ya.out = ys;
@@ -686,8 +711,9 @@ gridspt_status derive_order_div(const gridspt_plan_s* p, int m, float2* dk, floa
     za.codes[1] = z_code(3, 0, NI, 1);   // u_x = -i kx phi
     za.codes[2] = z_code(1, 0, NI, 2);   // u_y = -i ky phi
     za.codes[3] = z_code(2, 1, NI, 3);   // u_z = -i kz phi
-    CKP(PK_YEXP, fb * (3 + 4), s, launch_yexp(p->geo, ya, s), "y expansion (divergence form)");
-    CKP(PK_ZEXP, fb * (4 + 4), s, launch_zexp(p->geo, za, s), "z expansion (divergence form)");
+    const double fz = za.band > 0 ? (double)za.band / p->geo.M : 1.0;
+    CKP(PK_YEXP, fb * (3 * fy_in + 4 * fy_out), s, launch_yexp(p->geo, ya, s), "y expansion (divergence form)");
+    CKP(PK_ZEXP, fb * (4 * fz + 4), s, launch_zexp(p->geo, za, s), "z expansion (divergence form)");
     return GRIDSPT_OK;
 }
 

@@ -60,6 +60,8 @@ struct XExpArgs {
     long long shell_hi;
     int band;              // > 0: only columns with |ky| < band and kz < band are
                            //      transformed and written (all other outputs zero)
+    long long s2_in = -1;  // backward pass (fwd_first = 0), >= 0: input modes with
+                           //      |s|^2 > s2_in are taken as zero (the cut on delta_1)
     // divergence-form sources (fwd_first = 1): when div_in is set, the inputs are
     // the y-transformed V_x, V_y, V_z, S at div_in + q * div_stride (q = 0..3);
     // after the forward x transform A = i k . V, B = -(k^2 / 2) S and
@@ -78,7 +80,9 @@ struct YZExpArgs {
     int codes[kMaxExpOut]; // outputs of the same input must be consecutive; each
                            // is written to out + slot * out_stride
     int band;              // y pass, > 0: inputs nonzero only at |ky| < band and
-                           //      kz < band; only kz < band columns are formed
+                           //      kz < band; only kz < band columns are formed.
+                           // z pass, > 0: inputs nonzero only at kz < band (only
+                           //      those are read); every real output is formed
 };
 
 struct IcArgs {

@@ -274,6 +274,10 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
         for (int i = 0; i < E; ++i) {
             xd[i] = act ? args.src0[colofs + (p + P * i) * estride] : make_float2(0.f, 0.f);
             xt[i] = (act && two) ? args.src1[colofs + (p + P * i) * estride] : xd[i];
+            if (MODE == 0 && args.s2_in >= 0) {          // the cut on delta_1
+                const int sx = signed_idx(p + P * i, N);
+                if ((long long)(sx * sx + syz) > args.s2_in) xd[i] = xt[i] = make_float2(0.f, 0.f);
+            }
         }
         __syncthreads();
     }
@@ -491,6 +495,7 @@ k_yexp2(YZExpArgs args, const float2* __restrict__ twg, float kF) {
 template <int N, int TZ, bool PREFETCH>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
 k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+    const int B = args.band;                     // > 0: inputs nonzero only at kz < B
     constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NT = TZ * P;
     extern __shared__ float2 sm[];
     float2* tw = sm;
@@ -530,8 +535,8 @@ k_zexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int k = p + P * i;
-            float2 Xk = colp[k];
-            float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
+            float2 Xk = (B <= 0 || k < B) ? colp[k] : make_float2(0.f, 0.f);
+            float2 Xm = (k && (B <= 0 || M - k < B)) ? colp[M - k] : make_float2(0.f, 0.f);
             if (g) {
                 const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
                 Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);
@@ -586,6 +591,7 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
     const YZExpArgs& z = args.z;
+    constexpr int B = 0;                         // pair launches never have a band
     // real fields as rows of M float2 (cells 2k, 2k + 1)
     const long long fstride2 = args.cells / 2;
     float2 accA[NT][E], accB[NT][E];
@@ -619,8 +625,8 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int k = p + P * i;
-            float2 Xk = colp[k];
-            float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
+            float2 Xk = (B <= 0 || k < B) ? colp[k] : make_float2(0.f, 0.f);
+            float2 Xm = (k && (B <= 0 || M - k < B)) ? colp[M - k] : make_float2(0.f, 0.f);
             if (g) {
                 const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
                 Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);
@@ -775,6 +781,9 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     float2* wpt = wbase + 2 * WIN;                                                 // [MAXP][RW][M] partners
     float2* xrow = wbase + WIN * (NT ? 2 + C::MAXP : 2) + r * C::XROW;              // this row's exchange buffer
     const YZExpArgs& z = args.z;
+    // > 0: inputs nonzero only at kz < B (only those are loaded); only the
+    // store-only launch of order 1 has a band, the pair forms fold it away
+    const int B = NT == 0 ? z.band : 0;
     const long long rows = (long long)N * N;
     const long long groups = rows / RW;
     const long long gstride = (long long)gridDim.x * kRowWarps;
@@ -815,9 +824,12 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                     const float4* src = reinterpret_cast<const float4*>(z.in + in * z.in_stride + row0 * M);
                     float4 v[WIN / 64];
 #pragma unroll
-                    for (int u = 0; u < WIN / 64; ++u) v[u] = __ldg(src + lane + 32 * u);
+                    for (int u = 0; u < WIN / 64; ++u)
+                        if (B <= 0 || (2 * (lane + 32 * u)) % M < B) v[u] = __ldg(src + lane + 32 * u);
 #pragma unroll
-                    for (int u = 0; u < WIN / 64; ++u) reinterpret_cast<float4*>(wbase + buf * WIN)[lane + 32 * u] = v[u];
+                    for (int u = 0; u < WIN / 64; ++u)
+                        if (B <= 0 || (2 * (lane + 32 * u)) % M < B)
+                            reinterpret_cast<float4*>(wbase + buf * WIN)[lane + 32 * u] = v[u];
                     __syncwarp();
                 }
                 cur = in;
@@ -831,7 +843,9 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                     const float2* src = z.in + nin * z.in_stride + nrow0 * M;
                     float2* dst = wbase + (buf ^ 1) * WIN;
 #pragma unroll
-                    for (int u = 0; u < WIN / 64; ++u) cp_async16(dst + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
+                    for (int u = 0; u < WIN / 64; ++u)
+                        if (B <= 0 || (2 * (lane + 32 * u)) % M < B)
+                            cp_async16(dst + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
                     have_next = true;
                 }
             }
@@ -841,8 +855,8 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int k = p + P * i;
-                float2 Xk = colp[k];
-                float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
+                float2 Xk = (B <= 0 || k < B) ? colp[k] : make_float2(0.f, 0.f);
+                float2 Xm = (k && (B <= 0 || M - k < B)) ? colp[M - k] : make_float2(0.f, 0.f);
                 if (g) {
                     const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
                     Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);

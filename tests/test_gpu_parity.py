@@ -210,6 +210,21 @@ def test_oblique_plane_wave_closed_form_large_grid(N, n_max, s):
     torch.cuda.empty_cache()
 
 
+def test_modes_of_delta1_above_the_cut_are_ignored():
+    """run_orders applies delta_1's cut: a mode added above it (inside and
+    outside the band of columns the order-1 passes move) changes nothing."""
+    N, L, n_max = 48, 300.0, 4
+    plan = g.Plan(N, n_max, L)
+    d1 = g.make_linear_field(plan, [91])
+    ref = g.run_orders(plan, d1)
+    r = N / (n_max + 1)                          # cut radius in units of k_F
+    dirty = d1.clone()
+    dirty[0, 9, 3, 2] = 0.5 + 0.25j              # |s|^2 = 94 > r^2, every component inside the band
+    dirty[0, 2, 1, 15] = 0.25                    # kz beyond the band
+    assert 9 * 9 + 3 * 3 + 2 * 2 > r * r and 15 > r
+    assert torch.equal(g.run_orders(plan, dirty), ref)
+
+
 def test_resume_equals_full_run_bitwise():
     N, L, n_max = 64, 400.0, 5
     plan = g.Plan(N, n_max, L)
