@@ -78,3 +78,24 @@ def linear_pk(k, cosmo, A=None):
 
 
 DEFAULT_COSMO = {"omega_m": 0.3, "h": 0.7, "n_s": 0.96, "sigma8": 0.8, "gamma": 0.0}
+
+
+def growth_factor(z, cosmo, n_intervals=1 << 16):
+    """Linear growth factor D_+(z) / D_+(0) of a flat LCDM background (the
+    D_+ of Sec. II.A and of delta_SPT = sum D_+^i delta_i, Sec. III.A):
+        D(a) = (5 Omega_m / 2) E(a) int_0^a da' / (a' E(a'))^3,
+        E(a) = sqrt(Omega_m a^-3 + 1 - Omega_m)   (Heath 1977),
+    the integral by composite Simpson in a (the integrand vanishes like
+    a'^(3/2) at a' -> 0)."""
+    om = cosmo["omega_m"]
+
+    def D(a):
+        x = np.linspace(0.0, a, n_intervals + 1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            E = np.sqrt(om / x ** 3 + 1.0 - om)
+            f = np.where(x > 0, 1.0 / (x * E) ** 3, 0.0)
+        h = a / n_intervals
+        integral = h / 3.0 * (f[0] + f[-1] + 4.0 * f[1:-1:2].sum() + 2.0 * f[2:-1:2].sum())
+        return 2.5 * om * math.sqrt(om / a ** 3 + 1.0 - om) * integral
+
+    return D(1.0 / (1.0 + z)) / D(1.0)

@@ -175,3 +175,22 @@ def bispectrum_one_loop(d1, d2, d3, d4, L, edges):
         E, ntri = bispectrum_triple(a, b, c, L, edges)
         B = B + E
     return B, ntri
+
+
+def cross_correlation(a_k, b_k, L, edges):
+    """r(bin) = sum Re[a b*] / sqrt(sum |a|^2 sum |b|^2) over the modes of each
+    bin (Eqs. r_corr_nthPT and r_corr_sum_nth; the printed Re[a b] reads as
+    the cross-spectrum Re[a b*]); 0 for an empty bin."""
+    N = a_k.shape[0]
+    k, s2 = mode_k(N, L)
+    idx = bin_index(k, s2, edges)
+    nb = len(edges) - 1
+    r = np.zeros(nb)
+    for i in range(nb):
+        m = idx == i
+        if m.any():
+            ab = np.sum((a_k[m] * np.conj(b_k[m])).real)
+            aa = np.sum(np.abs(a_k[m]) ** 2)
+            bb = np.sum(np.abs(b_k[m]) ** 2)
+            r[i] = ab / math.sqrt(aa * bb) if aa > 0 and bb > 0 else 0.0
+    return r

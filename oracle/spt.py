@@ -246,3 +246,17 @@ def real_space_orders(delta1_k, L, n_max, kcut_nl=None):
         cdA, cdB, ctA, ctB = recursion_coefficients(n)
         out[n] = (cdA * A + cdB * B, ctA * A + ctB * B)
     return out
+
+
+def sum_orders(fields_k, D, R, L):
+    """delta_SPT(k) = W(k R) sum_{i=1}^{n} D^i delta_i(k) (Sec. III.A), with the
+    Gaussian filter W(x) = exp(-x^2 / 2) the paper applies before looking at
+    the fields (R = 0: no filter). fields_k: [delta_1, ..., delta_n] full grids."""
+    N = fields_k[0].shape[0]
+    kF = 2.0 * math.pi / L
+    sx, sy, sz = wave_indices(N)
+    k2 = kF * kF * (sx * sx + sy * sy + sz * sz).astype(np.float64)
+    out = np.zeros_like(fields_k[0])
+    for i, f in enumerate(fields_k, start=1):
+        out = out + D ** i * f
+    return out * np.exp(-0.5 * k2 * R * R)

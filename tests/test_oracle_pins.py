@@ -532,3 +532,63 @@ def test_one_loop_bispectrum_equals_enumeration_of_its_definition():
                     (d2, d2, d2), (d1, d1, d4), (d1, d4, d1), (d4, d1, d1)]:
         Bb = Bb + estimators.bispectrum_triple_brute(a, b, c, L, edges)[0]
     assert np.allclose(B, Bb, rtol=1e-10, atol=1e-12 * np.abs(Bb).max())
+
+
+# ------------------------------------------------- summed fields, correlation
+def test_growth_factor_eds_and_ode():
+    """D_+(z)/D_+(0): Einstein-de Sitter gives a = 1/(1+z) exactly; for LCDM the
+    integral form equals the growing solution of the linear growth ODE
+    D'' + (3/a + dlnE/da) D' - 1.5 Om / (a^5 E^2) D = 0 integrated from deep in
+    matter domination (D = a there)."""
+    from scipy.integrate import solve_ivp
+    eds = dict(cosmology.DEFAULT_COSMO, omega_m=1.0)
+    for z in (0.0, 0.5, 1.0, 3.0):
+        assert abs(cosmology.growth_factor(z, eds) - 1.0 / (1.0 + z)) < 1e-10
+    om = 0.3
+    E = lambda a: math.sqrt(om / a ** 3 + 1 - om)
+    dlnE = lambda a: -1.5 * om / a ** 4 / E(a) ** 2
+
+    def rhs(a, y):
+        D, dD = y
+        return [dD, -(3.0 / a + dlnE(a)) * dD + 1.5 * om / (a ** 5 * E(a) ** 2) * D]
+
+    a0 = 1e-4
+    sol = solve_ivp(rhs, (a0, 1.0), [a0, 1.0], rtol=1e-11, atol=1e-14, dense_output=True)
+    c = dict(cosmology.DEFAULT_COSMO, omega_m=om)
+    for z in (0.5, 1.0, 2.0):
+        ode = sol.sol(1.0 / (1.0 + z))[0] / sol.sol(1.0)[0]
+        assert abs(cosmology.growth_factor(z, c) - ode) < 1e-6
+
+
+def test_sum_orders_smooths_a_plane_wave_by_the_gaussian():
+    """One wave per order: the smoothed sum is sum_i D^i A_i e^{-k^2 R^2/2} cos(k.x)
+    at every cell (direct evaluation in real space)."""
+    N, L, R, D = 16, 100.0, 7.0, 0.6
+    waves = [((1, 2, 0), 0.3), ((2, 0, 1), 0.2)]
+    f1 = inputs.plane_waves(N, [waves[0]])
+    f2 = inputs.plane_waves(N, [waves[1]])
+    got = spt.backward(spt.sum_orders([f1, f2], D, R, L)).real
+    j = np.arange(N)
+    x, y, z = np.meshgrid(j, j, j, indexing="ij")
+    exp = 0.0
+    for i, ((s, A)) in enumerate(waves, start=1):
+        k2 = (2 * math.pi / L) ** 2 * sum(c * c for c in s)
+        exp = exp + D ** i * A * math.exp(-0.5 * k2 * R * R) * np.cos(2 * math.pi * (s[0] * x + s[1] * y + s[2] * z) / N)
+    assert np.abs(got - exp).max() < 1e-13
+
+
+def test_cross_correlation_limits_and_definition():
+    N, L = 16, 120.0
+    a = spt.forward(inputs.random_real((N, N, N), 41))
+    b = spt.forward(inputs.random_real((N, N, N), 42))
+    kF = 2 * math.pi / L
+    edges = [kF * e for e in (0.5, 2.5, 4.5, 7.5)]
+    assert np.allclose(estimators.cross_correlation(a, 3.0 * a, L, edges), 1.0, atol=1e-14)
+    assert np.allclose(estimators.cross_correlation(a, -a, L, edges), -1.0, atol=1e-14)
+    r = estimators.cross_correlation(a, b, L, edges)
+    assert np.all(np.abs(r) <= 1.0)
+    # against the estimator's power spectra: r = P_ab / sqrt(P_aa P_bb)
+    pab = estimators.power(a, b, L, edges)[0]
+    paa = estimators.power(a, a, L, edges)[0]
+    pbb = estimators.power(b, b, L, edges)[0]
+    assert np.allclose(r, pab / np.sqrt(paa * pbb), rtol=1e-12)
