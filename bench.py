@@ -266,6 +266,13 @@ def run_gpu(args, rank, world):
     for _ in range(args.steps):
         e2e_step()
     e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, dist, "cuda")
+    # the host -> device link rate of the same copy alone (it varies between
+    # machines and dominates the difference between e2e and the device timing)
+    ev0.record(stream)
+    d1.copy_(host_d1, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbps = d1.numel() * 8 / (ev0.elapsed_time(ev1) / 1e3) / 1e9
 
     # the same recursion (all B realisations) captured once as a CUDA graph and replayed
     graph = g.Batch([plan], [d1], spectra=[spectra], wss=[ws])
@@ -314,7 +321,8 @@ def run_gpu(args, rank, world):
         "clocks": clk,
         "e2e": {"value": work / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(d1.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
-                "ms_per_step": e2e_ms, "path": "delta_1(k) from pinned host -> run_orders -> estimators -> host"},
+                "ms_per_step": e2e_ms, "h2d_GBps": round(h2d_gbps, 1),
+                "path": "delta_1(k) from pinned host -> run_orders -> estimators -> host"},
         "cpu_baseline": cb,
         "autotune": tuning,
         "recursion_graph": {"ms_per_launch": round(graph_ms, 3), "realisations": B,

@@ -187,6 +187,38 @@ gridspt_status gridspt_power_noalloc(gridspt_plan plan, const void* a_k, const v
                                      const double* edges, double* p_out, int64_t* nk_out,
                                      gridspt_stream stream);
 
+/* Linear growth factor D_+(z) / D_+(0) of a flat LCDM background (Omega_Lambda
+ * = 1 - omega_m; the D_+ of Sec. II.A that weights order i by D_+^i):
+ *   D(a) = (5 Omega_m / 2) E(a) int_0^a da' / (a' E(a'))^3,
+ *   E(a) = sqrt(Omega_m a^-3 + 1 - Omega_m), a = 1 / (1 + z),
+ * host FP64 (composite Simpson, 2^16 intervals). Requires 0 < omega_m <= 1,
+ * z > -1; only cosmo->omega_m is used. */
+gridspt_status gridspt_growth_factor(const gridspt_cosmo* cosmo, double z, double* D);
+
+/* Summed density field of Sec. III.A, smoothed with the Gaussian filter the
+ * paper applies before comparing fields:
+ *   out_k(k) = exp(-k^2 R^2 / 2) sum_{i=1}^{n} D^i delta_i(k)
+ * for one realisation. delta1_k: device half spectrum; spectra: device
+ * float2[n_max-1][2][N][N][N/2] as gridspt_run_orders writes it for one
+ * realisation (may be NULL when n = 1); 1 <= n <= n_max; D: growth factor
+ * (e.g. from gridspt_growth_factor), R >= 0 in Mpc/h (0: no filter); out_k:
+ * device half spectrum (may not alias the inputs). FP32 sums with D^i formed
+ * in FP64 on the host; the filter in FP32. gridspt_c2r gives the field in real
+ * space. */
+gridspt_status gridspt_sum_orders(gridspt_plan plan, const void* delta1_k, const void* spectra, int32_t n,
+                                  double D, double R, void* out_k, gridspt_stream stream);
+
+/* Cross-correlation coefficient per shell (Sec. III.B, Eqs. r_corr_nthPT and
+ * r_corr_sum_nth with the cross-spectrum read as Re[a b*]):
+ *   r_out[i] = sum Re[a b*] / sqrt(sum |a|^2 sum |b|^2) over the modes of bin i,
+ * formed from three gridspt_power spectra (P_ab / sqrt(P_aa P_bb)); 0 for an
+ * empty bin. Bins as for gridspt_power; r_out: device double[nbins]; ws:
+ * gridspt_cross_correlation_workspace_size bytes of device scratch. */
+gridspt_status gridspt_cross_correlation_workspace_size(gridspt_plan plan, int32_t nbins, size_t* bytes);
+gridspt_status gridspt_cross_correlation(gridspt_plan plan, const void* a_k, const void* b_k, int32_t nbins,
+                                         const double* edges, double* r_out, void* ws, size_t ws_bytes,
+                                         gridspt_stream stream);
+
 /* Equilateral FFT shell bispectrum (Sec. III.B.1, Eq. bk_tree, measured with
  * an FFT shell estimator): for shell i,
  *   e_out[i]    = L^6 sum_x I_i[a](x)^2 I_i[b](x) / sum_x J_i(x)^3,

@@ -46,6 +46,12 @@ SIGNATURES = {
     "gridspt_bispectrum_workspace_size": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t)]),
     "gridspt_bispectrum": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gridspt_growth_factor": (c_int32, [ctypes.POINTER(GridsptCosmo), c_double, ctypes.POINTER(c_double)]),
+    "gridspt_sum_orders": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_double, c_void_p,
+                                     c_void_p]),
+    "gridspt_cross_correlation_workspace_size": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t)]),
+    "gridspt_cross_correlation": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_double),
+                                            c_void_p, c_void_p, c_size_t, c_void_p]),
     "gridspt_bispectrum_triple": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                             ctypes.POINTER(c_double), c_void_p, c_void_p, c_void_p, c_size_t,
                                             c_void_p]),

@@ -79,12 +79,12 @@ bool fault_inject(const char* what) {
 // ------------------------------------------------------------- profiling
 enum ProfKind {
     PK_IC, PK_XEXP, PK_XEXP_FWD, PK_YEXP, PK_ZEXP, PK_Y_FWD, PK_X_FWD, PK_ZR2C,
-    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_MLP_FWD, PK_MLP_BWD, PK_MLP_OPT, PK_COUNT
+    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_MLP_FWD, PK_MLP_BWD, PK_MLP_OPT, PK_FIELDS, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {
     "ic", "x_expand", "x_fwd_expand", "y_expand", "z_expand", "y_fwd", "x_fwd", "z_r2c",
     "product", "power", "bispec_final", "shell_x", "shell_y", "shell_z", "mlp_forward", "mlp_backward",
-    "mlp_update"};
+    "mlp_update", "sum_orders"};
 constexpr size_t kMaxProfRecs = 65536;
 
 struct ProfRec {
@@ -1249,6 +1249,94 @@ gridspt_status gridspt_power(gridspt_plan p, const void* a_k, const void* b_k, i
     return GRIDSPT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}
+
+extern "C" {
+
+gridspt_status gridspt_growth_factor(const gridspt_cosmo* c, double z, double* D) {
+    g_err[0] = 0;
+    if (!c || !D) return fail(GRIDSPT_E_INVALID, "cosmo/D is NULL");
+    const double om = c->omega_m;
+    if (!(om > 0.0 && om <= 1.0) || !(z > -1.0) || !std::isfinite(z))
+        return fail(GRIDSPT_E_INVALID, "need 0 < omega_m <= 1 and z > -1");
+    // D(a) = 5/2 Om E(a) int_0^a da' (a' E(a'))^-3, E = sqrt(Om a^-3 + 1 - Om): composite Simpson
+    auto growth = [om](double a) {
+        const int n = 1 << 16;
+        const double h = a / n;
+        double sum = 0.0;
+        for (int i = 1; i <= n; ++i) {   // f(0) = 0
+            const double x = i * h;
+            const double e = std::sqrt(om / (x * x * x) + 1.0 - om);
+            const double f = 1.0 / ((x * e) * (x * e) * (x * e));
+            sum += (i == n ? 1.0 : (i % 2 ? 4.0 : 2.0)) * f;
+        }
+        return 2.5 * om * std::sqrt(om / (a * a * a) + 1.0 - om) * (h / 3.0) * sum;
+    };
+    *D = growth(1.0 / (1.0 + z)) / growth(1.0);
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_sum_orders(gridspt_plan p, const void* delta1_k, const void* spectra, int32_t n, double D,
+                                  double R, void* out_k, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (n < 1 || n > p->d.n_max) return fail(GRIDSPT_E_INVALID, "n=%d outside [1, %d]", n, p->d.n_max);
+    if (!delta1_k || !out_k || (n >= 2 && !spectra)) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    if (!aligned16(delta1_k) || !aligned16(out_k) || (spectra && !aligned16(spectra)))
+        return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
+    if (!std::isfinite(D) || !(R >= 0.0) || !std::isfinite(R)) return fail(GRIDSPT_E_INVALID, "need finite D, R >= 0");
+    if (gridspt_status st = set_device(p)) return st;
+    const long long F = field_c(p);
+    SumOrdersArgs a{};
+    a.n = n;
+    a.N = p->geo.N;
+    a.out = static_cast<float2*>(out_k);
+    a.r2kf2 = (float)((R * p->geo.kF) * (R * p->geo.kF));
+    double c = 1.0;
+    for (int i = 1; i <= n; ++i) {
+        c *= D;
+        a.coef[i - 1] = (float)c;
+        a.field[i - 1] = i == 1 ? static_cast<const float2*>(delta1_k)
+                                : static_cast<const float2*>(spectra) + (long long)(i - 2) * 2 * F;
+    }
+    CKP(PK_FIELDS, 4.0 * (double)field_floats(p) * (n + 1), (cudaStream_t)stream,
+        launch_sum_orders(a, (cudaStream_t)stream), "summed orders");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_cross_correlation_workspace_size(gridspt_plan p, int32_t nbins, size_t* bytes) {
+    if (check_plan(p) || !bytes) return fail(GRIDSPT_E_INVALID, "plan/bytes is NULL");
+    size_t pw = 0;
+    if (gridspt_status st = gridspt_power_workspace_size(p, nbins, &pw)) return st;
+    *bytes = align256(pw) + align256(3 * (size_t)nbins * sizeof(double));
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_cross_correlation(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins,
+                                         const double* edges, double* r_out, void* ws, size_t ws_bytes,
+                                         gridspt_stream stream) {
+    g_err[0] = 0;
+    if (check_plan(p)) return GRIDSPT_E_INVALID;
+    if (!a_k || !b_k || !r_out || !ws) return fail(GRIDSPT_E_INVALID, "NULL argument");
+    size_t need = 0, pw = 0;
+    if (gridspt_status st = gridspt_cross_correlation_workspace_size(p, nbins, &need)) return st;
+    if (ws_bytes < need) return fail(GRIDSPT_E_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    gridspt_power_workspace_size(p, nbins, &pw);
+    char* base = static_cast<char*>(ws);
+    double* pp = reinterpret_cast<double*>(base + align256(pw));
+    const struct { const void* x; const void* y; double* out; } terms[3] = {
+        {a_k, b_k, pp}, {a_k, a_k, pp + nbins}, {b_k, b_k, pp + 2 * nbins}};
+    for (const auto& t : terms)
+        if (gridspt_status st = gridspt_power(p, t.x, t.y, nbins, edges, t.out, nullptr, ws, align256(pw), stream))
+            return st;
+    CK(launch_rcorr(pp, pp + nbins, pp + 2 * nbins, nbins, r_out, (cudaStream_t)stream), "correlation coefficient");
+    return GRIDSPT_OK;
+}
+
 gridspt_status gridspt_power_noalloc(gridspt_plan p, const void* a_k, const void* b_k, int32_t nbins,
                                      const double* edges, double* p_out, int64_t* nk_out,
                                      gridspt_stream stream) {
@@ -1271,10 +1359,6 @@ gridspt_status gridspt_power_noalloc(gridspt_plan p, const void* a_k, const void
         launch_power(p->geo, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k), bs, scratch,
                      p_out, nk_out, vol, (cudaStream_t)stream), "power launch");
     return GRIDSPT_OK;
-}
-
-namespace {
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }
 
 gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan p, int32_t nbins, size_t* bytes) {

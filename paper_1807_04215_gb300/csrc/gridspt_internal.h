@@ -168,6 +168,20 @@ struct ProductDivArgs {
 };
 cudaError_t launch_product_div(const Geo& g, const ProductDivArgs& a, cudaStream_t s);
 
+// delta_SPT = W(k R) sum_i coef[i] field[i] over one half spectrum (k_fields.cu)
+struct SumOrdersArgs {
+    const float2* field[kMaxOrder];
+    float coef[kMaxOrder];
+    int n;                 // number of fields
+    int N;
+    float r2kf2;           // (R k_F)^2; 0: no filter
+    float2* out;
+};
+cudaError_t launch_sum_orders(const SumOrdersArgs& a, cudaStream_t s);
+// r[i] = pab[i] / sqrt(paa[i] pbb[i]) (0 where the denominator vanishes), nbins <= 64
+cudaError_t launch_rcorr(const double* pab, const double* paa, const double* pbb, int nbins, double* r,
+                         cudaStream_t s);
+
 // Power: per-block partial sums (2 * nbins doubles per block) then a fixed-order
 // final reduction. blocks: number of partial-sum blocks (power_blocks()).
 int power_blocks(const Geo& g);

@@ -89,6 +89,15 @@ def linear_amplitude(cosmo=None):
     return A.value
 
 
+def growth_factor(z, cosmo=None):
+    """D_+(z) / D_+(0) of a flat LCDM background (gridspt_growth_factor)."""
+    lib = _lib.load()
+    c = _lib.GridsptCosmo(**(cosmo or DEFAULT_COSMO))
+    D = ctypes.c_double()
+    _lib.check("gridspt_growth_factor", lib.gridspt_growth_factor(ctypes.byref(c), float(z), ctypes.byref(D)))
+    return D.value
+
+
 def make_linear_field(plan, seeds, cosmo=None, out=None):
     seeds = [int(s) for s in seeds]
     if len(seeds) != plan.batch:
@@ -277,6 +286,38 @@ def bispectrum(plan, a, b, edges, ws=None):
                plan.lib.gridspt_bispectrum(plan.handle, _ptr(a), _ptr(b), nb, e, _ptr(E), _ptr(nt), _ptr(ws),
                                            ws.numel(), _stream()))
     return E, nt
+
+
+def sum_orders(plan, delta1, spectra, n, D=1.0, R=0.0, out=None):
+    """delta_SPT(k) = exp(-k^2 R^2 / 2) sum_{i<=n} D^i delta_i(k) for one
+    realisation: delta1 [N][N][N/2], spectra [n_max-1][2][N][N][N/2]."""
+    plan._check_half(delta1, (), "delta1")
+    if n >= 2:
+        plan._check_half(spectra, (plan.n_max - 1, 2), "spectra")
+    if out is None:
+        out = torch.empty(plan.half_shape(), dtype=torch.complex64, device="cuda")
+    plan._check_half(out, (), "out")
+    _lib.check("gridspt_sum_orders",
+               plan.lib.gridspt_sum_orders(plan.handle, _ptr(delta1), _ptr(spectra) if n >= 2 else None, int(n),
+                                           float(D), float(R), _ptr(out), _stream()))
+    return out
+
+
+def cross_correlation(plan, a, b, edges, ws=None):
+    """Cross-correlation coefficient r = P_ab / sqrt(P_aa P_bb) per bin."""
+    plan._check_half(a, (), "a")
+    plan._check_half(b, (), "b")
+    e, nb = _edges(edges)
+    if ws is None:
+        size = ctypes.c_size_t()
+        _lib.check("gridspt_cross_correlation_workspace_size",
+                   plan.lib.gridspt_cross_correlation_workspace_size(plan.handle, nb, ctypes.byref(size)))
+        ws = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+    r = torch.empty(nb, dtype=torch.float64, device="cuda")
+    _lib.check("gridspt_cross_correlation",
+               plan.lib.gridspt_cross_correlation(plan.handle, _ptr(a), _ptr(b), nb, e, _ptr(r), _ptr(ws), ws.numel(),
+                                                  _stream()))
+    return r
 
 
 def bispectrum_triple(plan, a, b, c, edges, ws=None):

@@ -76,3 +76,22 @@ def test_linear_amplitude_matches_oracle(lib):
         assert lib.gridspt_linear_amplitude(ctypes.byref(cc), ctypes.byref(A)) == 0
         ref = cosmology.amplitude(dict(c))
         assert abs(A.value / ref - 1) < 1e-10
+
+
+def test_growth_factor_matches_oracle(lib):
+    """The library's FP64 growth factor (its own Simpson rule in C) against the
+    oracle's, and the invalid arguments it rejects."""
+    from oracle import cosmology
+    from paper_1807_04215_gb300 import _lib
+    for om in (0.3, 0.25, 1.0):
+        c = dict(cosmology.DEFAULT_COSMO, omega_m=om)
+        cc = _lib.GridsptCosmo(**c)
+        for z in (0.0, 0.5, 1.0, 3.0):
+            D = ctypes.c_double()
+            assert lib.gridspt_growth_factor(ctypes.byref(cc), z, ctypes.byref(D)) == 0
+            assert abs(D.value - cosmology.growth_factor(z, c)) < 1e-12
+    D = ctypes.c_double()
+    bad = _lib.GridsptCosmo(**dict(cosmology.DEFAULT_COSMO, omega_m=0.0))
+    assert lib.gridspt_growth_factor(ctypes.byref(bad), 0.5, ctypes.byref(D)) == 1
+    good = _lib.GridsptCosmo(**cosmology.DEFAULT_COSMO)
+    assert lib.gridspt_growth_factor(ctypes.byref(good), -1.0, ctypes.byref(D)) == 1
