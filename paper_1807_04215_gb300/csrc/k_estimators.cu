@@ -12,6 +12,10 @@
 // contiguous: a segmented shuffle scan sums each run and its last lane adds
 // the run to the warp's FP64 accumulator (one writer per bin per step). Warps
 // and blocks are then summed in a fixed order: results are bitwise repeatable.
+// The scan runs in FP32 with each addition's rounding error carried exactly
+// (Knuth's two-sum) and added at the tail, so a run's sum is good to about
+// FP32^2 while the FP64 pipe (a small fraction of the FP32 rate here) sees
+// one addition per run; the mode counts are exact in FP32.
 //
 // Bispectrum (Eq. bk_tree, FFT shell estimator): the per-shell sums are formed
 // in k_zshell (k_transform.cuh); the final fixed-order reduction is here.
@@ -65,29 +69,34 @@ k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins
                 }
                 bin = lo;
             }
-            double v = 0.0, c = 0.0;
+            float v = 0.f, e = 0.f, c = 0.f;     // sum, carried rounding error, weight
             if (bin >= 0 && bin < nb) {
                 const float2 x = ar[kz], y = br[kz];
                 const float wgt = kz == 0 ? 1.f : 2.f;
-                v = (double)(wgt * fmaf(x.x, y.x, x.y * y.y));
-                c = (double)wgt;
+                v = wgt * fmaf(x.x, y.x, x.y * y.y);
+                c = wgt;
             }
             // segmented inclusive scan over runs of equal bin
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const double ov = __shfl_up_sync(0xffffffffu, v, off);
-                const double oc = __shfl_up_sync(0xffffffffu, c, off);
+                const float ov = __shfl_up_sync(0xffffffffu, v, off);
+                const float oe = __shfl_up_sync(0xffffffffu, e, off);
+                const float oc = __shfl_up_sync(0xffffffffu, c, off);
                 const int ob = __shfl_up_sync(0xffffffffu, bin, off);
                 if (lane >= off && ob == bin) {
-                    v += ov;
+                    const float t = __fadd_rn(v, ov);            // two-sum: t + r = v + ov exactly
+                    const float bv = __fsub_rn(t, v);
+                    const float r = __fadd_rn(__fsub_rn(v, __fsub_rn(t, bv)), __fsub_rn(ov, bv));
+                    v = t;
+                    e = __fadd_rn(__fadd_rn(e, oe), r);
                     c += oc;
                 }
             }
             const int nxt = __shfl_down_sync(0xffffffffu, bin, 1);
             const bool tail = (lane == 31) || (nxt != bin);
             if (tail && bin >= 0 && bin < nb) {
-                acc[w][bin] += v;
-                acc[w][kMaxBins + bin] += c;
+                acc[w][bin] += (double)v + (double)e;
+                acc[w][kMaxBins + bin] += (double)c;
             }
             __syncwarp();
         }

@@ -1086,7 +1086,6 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* t3 = sm + N;
-    __shared__ double r1[TZ], r2[TZ];
     static_assert(NT % 32 == 0, "block of whole warps");
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
@@ -1127,58 +1126,59 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
 #pragma unroll
     for (int f = 0; f < NF; ++f) fft_column<M, +1, N>(x[f], p, t3 + f * TZ * PITCH + c * PITCH, 1, tw);
     constexpr int ND = TRI ? 3 : 2;                   // data fields; J follows when NF > ND
-    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
-    if (row0 + c < rows) {
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            kahan_add2(s1, c1, cell_mul3(x[0][i], TRI ? x[1][i] : x[0][i], x[TRI ? 2 : 1][i]));   // cells 2n, 2n + 1
-            if constexpr (NF > ND) kahan_add2(s2, c2, cell_mul3(x[NF - 1][i], x[NF - 1][i], x[NF - 1][i]));
-        }
-    }
-    const double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
-    // fixed-order reduction, grouped as in the warp-row kernel: per row a
-    // shuffle tree over its P threads, then the block's rows in order
+    // fixed-order reduction, grouped as in the warp-row kernel: 32 chains
+    // (slot l = r P + p: rows c = r, r + 32/P, ... of the block in order, each
+    // row's elements i in order) of Kahan FP32 sums, then one FP64 shuffle tree
+    // over the 32 chains. The terms go through shared memory so that one warp
+    // can run the chains.
     __syncthreads();                                   // tiles are no longer read
-    double* red = reinterpret_cast<double*>(t3);       // [2][TZ][P]
-    red[c * P + p] = d1;
-    red[NT + c * P + p] = d2;
-    __syncthreads();
-    const int w = tid >> 5, lane = tid & 31;
-    for (int rr = w; rr < TZ; rr += NT / 32 > 0 ? NT / 32 : 1) {
-        double a = lane < P ? red[rr * P + lane] : 0.0, b = lane < P ? red[NT + rr * P + lane] : 0.0;
-        for (int q = lane + 32; q < P; q += 32) {     // rows longer than a warp (P = 64)
-            a += red[rr * P + q];
-            b += red[NT + rr * P + q];
-        }
+    float* T1 = reinterpret_cast<float*>(t3);          // [TZ][P][E] terms
+    float* T2 = T1 + TZ * P * E;
+    const bool live = row0 + c < rows;
 #pragma unroll
-        for (int off = (P < 32 ? P : 32) / 2; off > 0; off >>= 1) {
+    for (int i = 0; i < E; ++i) {
+        T1[(c * P + p) * E + i] = live ? cell_mul3(x[0][i], TRI ? x[1][i] : x[0][i], x[TRI ? 2 : 1][i]) : 0.f;
+        if constexpr (NF > ND) T2[(c * P + p) * E + i] = live ? cell_mul3(x[NF - 1][i], x[NF - 1][i], x[NF - 1][i]) : 0.f;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+        auto chain = [&](int cc, int pp) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                kahan_add2(s1, c1, T1[(cc * P + pp) * E + i]);
+                if constexpr (NF > ND) kahan_add2(s2, c2, T2[(cc * P + pp) * E + i]);
+            }
+        };
+        if constexpr (P <= 32) {
+            constexpr int RWS = 32 / P;
+            for (int cc = tid / P; cc < TZ; cc += RWS) chain(cc, tid % P);
+        } else {                                       // rows longer than a warp (P = 64)
+            for (int cc = 0; cc < TZ; ++cc)
+                for (int pp = tid; pp < P; pp += 32) chain(cc, pp);
+        }
+        double a = (double)s1 - (double)c1, b = (double)s2 - (double)c2;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, off);
             b += __shfl_down_sync(0xffffffffu, b, off);
         }
-        if (lane == 0) {
-            r1[rr] = a;
-            r2[rr] = b;
+        if (tid == 0) {
+            partial[2 * blockIdx.x] = a;
+            partial[2 * blockIdx.x + 1] = b;
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int i = 0; i < TZ; ++i) {
-            a += r1[i];
-            b += r2[i];
-        }
-        partial[2 * blockIdx.x] = a;
-        partial[2 * blockIdx.x + 1] = b;
     }
 }
 
 // Warp-row form of k_zshell: one z row per P lanes, the band-limited inputs
 // (kz < band) read straight into registers by coalesced loads, the transform
 // exchanged through a per-warp buffer. Each warp sums a group of G = TZZ0
-// consecutive rows (G is the tile kernel's block height): per-lane Kahan sums,
-// a shuffle tree over the row's P lanes, rows added in order, one FP64
-// partial pair per group. Terms, tree and order are those of the tile kernel,
-// so the partials are bitwise equal.
+// consecutive rows (G is the tile kernel's block height): every lane keeps one
+// Kahan FP32 sum over its rows of the group (in row order), then one FP64
+// shuffle tree over the 32 lanes gives the group's partial pair. The FP64
+// pipe (a small fraction of the FP32 rate on this GPU) sees one tree per
+// group instead of one per row. Terms, chains and tree are those of the tile
+// kernel, so the partials are bitwise equal.
 template <int N, int NF, bool TRI>
 __global__ void __launch_bounds__(kRowWarps * 32, 2)
 k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
@@ -1198,7 +1198,7 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
     const long long groups = (long long)N * N / G;
     for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups;
          grp += (long long)gridDim.x * kRowWarps) {
-        double acc1 = 0.0, acc2 = 0.0;
+        float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;   // this lane's chains over its rows
         for (int rr = 0; rr < G; rr += RW) {
             const long long row = grp * G + rr + r;
             // one band-limited row of field f, packed and transformed to real cells
@@ -1217,7 +1217,6 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
                 fft_row<M, +1>(x, p, xrow, twl);
             };
             constexpr int ND = TRI ? 3 : 2;               // data fields; J follows when NF > ND
-            float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
             {
                 float2 x[ND][E];
 #pragma unroll
@@ -1231,29 +1230,20 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
 #pragma unroll
                 for (int i = 0; i < E; ++i) kahan_add2(s2, c2, cell_mul3(xj[i], xj[i], xj[i]));
             }
-            double d1 = (double)s1 - (double)c1, d2 = (double)s2 - (double)c2;
+        }
+        double a = (double)s1 - (double)c1, b = (double)s2 - (double)c2;
 #pragma unroll
-            for (int off = P / 2; off > 0; off >>= 1) {
-                d1 += __shfl_down_sync(0xffffffffu, d1, off);
-                d2 += __shfl_down_sync(0xffffffffu, d2, off);
-            }
-#pragma unroll
-            for (int q = 0; q < RW; ++q) {                 // the warp's rows in order
-                acc1 += __shfl_sync(0xffffffffu, d1, q * P);
-                acc2 += __shfl_sync(0xffffffffu, d2, q * P);
-            }
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, off);
+            b += __shfl_down_sync(0xffffffffu, b, off);
         }
         if (lane == 0) {
-            partial[2 * grp] = acc1;
-            partial[2 * grp + 1] = acc2;
+            partial[2 * grp] = a;
+            partial[2 * grp + 1] = b;
         }
     }
 }
 
-// Warp-row form of k_zr2c (forward z pass of `count` fields, in place
-// allowed): each warp reads its rows into registers, transforms them, and
-// forms the half spectrum from the exchange buffer; arithmetic per element is
-// that of k_zr2c, so results are bitwise equal.
 template <int N>
 __global__ void __launch_bounds__(kRowWarps * 32, 2)
 k_zrow_r2c(const float2* in, float2* out, long long fstride, int count, const float2* __restrict__ twg,
