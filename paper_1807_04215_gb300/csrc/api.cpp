@@ -31,6 +31,8 @@ struct gridspt_plan_s {
     long long pb_top = -1;  // cache of the last power-launch byte count (profiling only)
     double pb_modes = 0.0;
     double* j3 = nullptr;   // device [kMaxBins]: sum_x J^3 per bispectrum shell (data independent)
+    double* ic_table = nullptr;   // device [ic_s2 + 1]: mode amplitude per |s|^2 (same allocation as j3)
+    long long ic_s2 = 0;
     int* status = nullptr;  // device status word (bounded waits that gave up)
     int j3_nb = 0;          // shells the cache holds (0: empty) and their thresholds
     int j3_thr[kMaxBins + 1] = {};
@@ -299,14 +301,18 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     }
     e = cudaMalloc(&p->tw, sizeof(float2) * N);
     if (e != cudaSuccess) { delete p; return fail(GRIDSPT_E_NOMEM, "twiddle table: %s", cudaGetErrorString(e)); }
+    // one small block: the shell cache (kMaxBins doubles), the status word (4
+    // ints) and the initial field's amplitude table (|s|^2 = 0..ic_s2)
+    p->ic_s2 = std::min<long long>(p->s2_lin, 3LL * (N / 2) * (N / 2));
     e = fault_inject("plan_alloc") ? cudaErrorMemoryAllocation
-                                   : cudaMalloc(&p->j3, sizeof(double) * kMaxBins + sizeof(int) * 4);
+                                   : cudaMalloc(&p->j3, sizeof(double) * (kMaxBins + 2 + p->ic_s2 + 1));
     if (e != cudaSuccess) {
         cudaFree(p->tw);
         delete p;
         return fail(GRIDSPT_E_NOMEM, "shell cache: %s", cudaGetErrorString(e));
     }
     p->status = reinterpret_cast<int*>(p->j3 + kMaxBins);
+    p->ic_table = p->j3 + kMaxBins + 2;
     p->geo.status = p->status;
     e = cudaMemset(p->status, 0, sizeof(int));
     if (e != cudaSuccess) { cudaFree(p->tw); cudaFree(p->j3); delete p; return cuda_fail(e, "status word"); }
@@ -360,7 +366,10 @@ gridspt_status gridspt_make_linear_field(gridspt_plan p, const gridspt_cosmo* c,
     a.n_s = c->n_s;
     a.gamma = gamma_of(c);
     a.inv_vol = 1.0 / (p->d.box * p->d.box * p->d.box);
-    a.s2_cut = p->s2_lin;
+    a.s2_cut = p->ic_s2;
+    a.table = p->ic_table;
+    a.kF = p->geo.kF;
+    CK(launch_ic_table(a, (cudaStream_t)stream), "ic amplitude table");
     for (int b = 0; b < p->d.batch; ++b) {
         a.out = static_cast<float2*>(delta1_k) + (long long)b * field_c(p);
         a.seed = seeds[b];

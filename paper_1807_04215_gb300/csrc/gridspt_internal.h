@@ -93,6 +93,8 @@ struct IcArgs {
     double gamma;
     double inv_vol;        // 1 / L^3
     long long s2_cut;      // keep 0 < |s|^2 <= s2_cut
+    double* table;         // [s2_cut + 1]: sqrt(P(k_F sqrt(s2)) / L^3) / sqrt(2), made by launch_ic_table
+    double kF;
 };
 
 // z expansion fused with accumulate-ahead pair products (Eq. recursion_formula):
@@ -140,6 +142,9 @@ struct BinSpec {
 };
 
 cudaError_t launch_ic(const Geo& g, const IcArgs& a, cudaStream_t s);
+// The mode amplitude of every |s|^2 <= s2_cut into a.table (once per call of
+// gridspt_make_linear_field; it depends on the spectrum, not on the seed).
+cudaError_t launch_ic_table(const IcArgs& a, cudaStream_t s);
 // One block waits on an mbarrier that nothing completes; the bounded wait gives
 // up and sets *status (exercises the timeout path without hanging the GPU).
 cudaError_t launch_wait_selftest(int* status, cudaStream_t s);

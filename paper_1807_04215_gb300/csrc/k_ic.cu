@@ -72,16 +72,33 @@ __global__ void k_ic(IcArgs a, int N, int M, double kF) {
             const double rad = sqrt(-2.0 * log(u1));
             double sn, cs;
             sincospi(2.0 * u2, &sn, &cs);
-            const double k = kF * sqrt((double)s2);
-            const double t = bbks_t(k / a.gamma);
-            const double pk = a.amp * pow(k, a.n_s) * t * t;
-            const double sd = sqrt(pk * a.inv_vol) * 0.70710678118654752440;
+            const double sd = a.table[s2];
             const double re = sd * rad * cs;
             const double im = sd * rad * sn;
             out = make_float2((float)re, (float)(canon ? im : -im));
         }
         a.out[idx] = out;
     }
+}
+
+// sqrt(P(k) / L^3) / sqrt(2) with P(k) = A k^n_s T_BBKS(k / Gamma)^2 at
+// k = k_F sqrt(s2), one thread per integer s2 (FP64).
+__global__ void k_ic_table(IcArgs a) {
+    const long long s2 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s2 > a.s2_cut) return;
+    double sd = 0.0;
+    if (s2 > 0) {
+        const double k = a.kF * sqrt((double)s2);
+        const double t = bbks_t(k / a.gamma);
+        const double pk = a.amp * pow(k, a.n_s) * t * t;
+        sd = sqrt(pk * a.inv_vol) * 0.70710678118654752440;
+    }
+    a.table[s2] = sd;
+}
+
+cudaError_t launch_ic_table(const IcArgs& a, cudaStream_t s) {
+    k_ic_table<<<(unsigned)((a.s2_cut + 1 + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ic(const Geo& g, const IcArgs& a, cudaStream_t s) {
