@@ -136,6 +136,34 @@ def test_recursion_matches_oracle(N, L, n_max, seed):
         assert e < tol, (n, which, e)
 
 
+@pytest.mark.parametrize("N,L,n_max,form", [(8, 60.0, 2, "nine_term"), (16, 100.0, 2, "nine_term"),
+                                              (12, 80.0, 3, "nine_term"), (8, 60.0, 3, "divergence"),
+                                              (12, 80.0, 2, "divergence")])
+def test_smallest_grids_and_lowest_orders(N, L, n_max, form):
+    """Degenerate ends: the smallest grids (N = 8, and N = 12 with its 6-point
+    row transform) and n_max = 2 (only the diagonal pair, no fused z-pass
+    pairs), in both source forms, against the oracle."""
+    plan = g.Plan(N, n_max, L, form=form)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, 5)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    sp = g.run_orders(plan, to_dev(ref1)[None])
+    oracle = spt.run_orders if form == "nine_term" else spt.run_orders_divergence
+    dk, tk = oracle(ref1, L, n_max)
+    for n in range(2, n_max + 1):
+        for which, ref in ((0, dk[n]), (1, tk[n])):
+            assert rms_rel(host(sp[0, n - 2, which]), ref) < (1e-5 if n == 2 else 1e-4), (n, which)
+
+
+def test_first_order_only_is_a_no_op():
+    """n_max = 1: there is nothing to form beyond delta_1; run_orders accepts an
+    empty spectra array and a zero-byte workspace."""
+    plan = g.Plan(16, 1, 100.0)
+    assert plan.workspace_size() == 0
+    d1 = g.make_linear_field(plan, [3])
+    sp = g.run_orders(plan, d1)
+    assert sp.numel() == 0
+
+
 @pytest.mark.slow
 def test_recursion_matches_oracle_128_fifth_order():
     errs = _parity_case(128, 500.0, 5, 21)
