@@ -24,7 +24,14 @@ struct Geo {
     int* status;            // device status word: set to 1 when a bounded wait gives up
 };
 
-// number of tile variants per pass (the autotuner times each)
+// number of tile variants per pass (the autotuner times each; results are
+// bitwise equal across them):
+//   column pass, x expansion: 0 wide tile, 1 narrow tile;
+//   y expansion: 0, 1 tiles, 2 TMA-staged tiles, 3 two columns per thread,
+//                4 narrow tile with cp.async prefetch of the next input;
+//   z expansion (and the fused pair products, bispectrum z pass): 0 tile,
+//                1 tile with cp.async prefetch, 2 warp rows;
+//   z forward pass: 0, 1 tiles, 2 warp rows.
 constexpr int kTuneVariants[TV_COUNT] = {2, 2, 5, 3, 3};
 
 // Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every

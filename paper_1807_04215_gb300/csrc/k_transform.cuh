@@ -28,10 +28,12 @@ namespace gridspt {
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-// Tile widths. Variant 0 is the default; variant 1 is the alternative the
-// autotuner also times (only instantiated separately for N >= 128). For the z
-// expansion the alternative keeps the tile width and instead prefetches the
-// next input tile with cp.async.
+// Tile widths. Variant 0 is the default; variant 1 is the alternative width
+// the autotuner also times (only instantiated separately for N >= 128). For
+// the z expansion variant 1 keeps the tile width and instead prefetches the
+// next input tile with cp.async. Further variants per pass are listed with
+// kTuneVariants (TMA-staged, column-pair and prefetching y passes; warp-row z
+// passes).
 template <int N>
 struct Cfg {
     static constexpr int M = N / 2;
