@@ -158,8 +158,10 @@ gridspt_status gridspt_r2c(gridspt_plan plan, const float* in_x, void* out_k, in
  *   a_k, b_k: device half spectra (one realisation each; b_k may equal a_k).
  *   edges:    HOST double[nbins+1], increasing, edges[nbins] <= k_Ny.
  *   p_out:    device double[nbins]; nk_out: device int64[nbins] (may be NULL).
- *   1 <= nbins <= 64. Products in FP32, shell sums in FP64, reduced in a
- *   fixed order (bitwise repeatable). Cross terms of the paper carry a factor
+ *   1 <= nbins <= 64. Products in FP32; runs of up to 32 consecutive modes
+ *   of a bin summed in FP32 with each addition's rounding error carried
+ *   (two-sum), the runs accumulated in FP64, all reduced in a fixed order
+ *   (bitwise repeatable). Cross terms of the paper carry a factor
  *   2: P_13 = 2 * gridspt_power(delta_1, delta_3). ws: device scratch of
  *   gridspt_power_workspace_size bytes (per-block partial sums). */
 gridspt_status gridspt_power_workspace_size(gridspt_plan plan, int32_t nbins, size_t* bytes);
@@ -227,7 +229,9 @@ gridspt_status gridspt_cross_correlation(gridspt_plan plan, const void* a_k, con
  * tree-level bispectrum is B_tree = 3 e_out for a = delta_1, b = delta_2.
  *   edges: HOST double[nbins+1] with edges[nbins] <= 2 k_Ny / 3 (no wrap);
  *   e_out, ntri_out: device double[nbins]; 1 <= nbins <= 64. FP32 fields,
- *   Kahan FP32 / FP64 sums. ws: gridspt_bispectrum_workspace_size bytes of
+ *   Kahan-compensated FP32 sums over row groups of cells, FP64 across groups,
+ *   fixed order. ws: gridspt_bispectrum_workspace_size bytes (4 fields and
+ *   the partial sums) of
  *   device scratch. sum_x J^3 does not depend on the data: the first call
  *   with a given set of shells computes it and keeps it in the plan (device
  *   memory), later calls with the same shells reuse it, so they must be
