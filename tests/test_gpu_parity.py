@@ -171,6 +171,18 @@ def test_recursion_matches_oracle_128_fifth_order():
         assert e < (1e-5 if n == 2 else 1e-4), (n, which, e)
 
 
+def test_recursion_with_a_cut_above_nyquist_matches_oracle():
+    """A linear cut past every grid mode (0.99 sqrt(3) k_Ny): order 1 moves every
+    column (the band covers the grid) and the initial field's amplitude table
+    stops at the largest |s|^2 on the grid; products fold, identically on both
+    sides."""
+    N, L = 24, 150.0
+    kny = math.pi * N / L
+    errs = _parity_case(N, L, 3, 61, kcut_lin=0.99 * math.sqrt(3.0) * kny)
+    for (n, which), e in errs.items():
+        assert e < (1e-5 if n == 2 else 1e-4), (n, which, e)
+
+
 def test_recursion_with_nonlinear_cut_matches_oracle():
     kF = 2 * math.pi / 300.0
     errs = _parity_case(48, 300.0, 4, 31, kcut_nl=kF * 14.5, kcut_lin=kF * 9.0)
