@@ -24,7 +24,8 @@ using namespace gridspt;
 struct gridspt_plan_s {
     gridspt_desc d;
     Geo geo;
-    float2* tw = nullptr;   // device, N entries
+    float2* tw = nullptr;   // device: N entries, then the tables of the smaller sizes (sub_off)
+    long long sub_off[kNumSizes] = {};   // offset in tw of the table of kSizes[i] < N, else -1
     long long s2_lin;       // keep 0 < |s|^2 <= s2_lin in delta_1
     long long s2_nl;        // < 0: no cut on higher orders
     int device = 0;
@@ -81,12 +82,13 @@ bool fault_inject(const char* what) {
 // ------------------------------------------------------------- profiling
 enum ProfKind {
     PK_IC, PK_XEXP, PK_XEXP_FWD, PK_YEXP, PK_ZEXP, PK_Y_FWD, PK_X_FWD, PK_ZR2C,
-    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_MLP_FWD, PK_MLP_BWD, PK_MLP_OPT, PK_FIELDS, PK_COUNT
+    PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_MLP_FWD, PK_MLP_BWD, PK_MLP_OPT, PK_FIELDS,
+    PK_BGATHER, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {
     "ic", "x_expand", "x_fwd_expand", "y_expand", "z_expand", "y_fwd", "x_fwd", "z_r2c",
     "product", "power", "bispec_final", "shell_x", "shell_y", "shell_z", "mlp_forward", "mlp_backward",
-    "mlp_update", "sum_orders"};
+    "mlp_update", "sum_orders", "shell_grid"};
 constexpr size_t kMaxProfRecs = 65536;
 
 struct ProfRec {
@@ -294,12 +296,21 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     }
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
-    std::vector<float2> tw(N);
-    for (int j = 0; j < N; ++j) {
-        const double a = 2.0 * M_PI * (double)j / (double)N;
-        tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    // roots of unity of size N, then of every smaller supported size (the
+    // bispectrum evaluates band-limited shells on smaller grids)
+    std::vector<float2> tw;
+    auto roots = [&tw](int n) {
+        for (int j = 0; j < n; ++j) {
+            const double a = 2.0 * M_PI * (double)j / (double)n;
+            tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+    };
+    roots(N);
+    for (int i = 0; i < kNumSizes; ++i) {
+        p->sub_off[i] = kSizes[i] < N ? (long long)tw.size() : -1;
+        if (kSizes[i] < N) roots(kSizes[i]);
     }
-    e = cudaMalloc(&p->tw, sizeof(float2) * N);
+    e = cudaMalloc(&p->tw, sizeof(float2) * tw.size());
     if (e != cudaSuccess) { delete p; return fail(GRIDSPT_E_NOMEM, "twiddle table: %s", cudaGetErrorString(e)); }
     // one small block: the shell cache (kMaxBins doubles), the status word (4
     // ints) and the initial field's amplitude table (|s|^2 = 0..ic_s2)
@@ -316,7 +327,7 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     p->geo.status = p->status;
     e = cudaMemset(p->status, 0, sizeof(int));
     if (e != cudaSuccess) { cudaFree(p->tw); cudaFree(p->j3); delete p; return cuda_fail(e, "status word"); }
-    e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(p->tw); cudaFree(p->j3); delete p; return cuda_fail(e, "twiddle upload"); }
     p->geo.tw = p->tw;
     *out = p;
@@ -1381,13 +1392,35 @@ gridspt_status gridspt_bispectrum_workspace_size(gridspt_plan p, int32_t nbins, 
 
 namespace {
 
-// Shell fields of one bispectrum shell: I_a, I_b (, I_c) and, without a cached
-// sum J^3, J, transformed along x (pruned to |ky|, kz < band) and y into
-// out[f] (stride fstride); the z pass follows fused with the sums.
-gridspt_status shell_fields(const gridspt_plan_s* p, const float2* a, const float2* b, const float2* c, bool has_j,
+// Geometry of the grid of size S <= N that shares the plan's box (same k_F,
+// tile variants and status word) for the band-limited bispectrum shells.
+Geo sub_geo(const gridspt_plan_s* p, int S) {
+    Geo g = p->geo;
+    if (S == p->geo.N) return g;
+    for (int i = 0; i < kNumSizes; ++i)
+        if (kSizes[i] == S && p->sub_off[i] >= 0) g.tw = p->tw + p->sub_off[i];
+    g.N = S;
+    g.M = S / 2;
+    return g;
+}
+
+// Grid on which a shell with every component |s_a| < band is evaluated: the
+// smallest supported size S > 3 (band - 1) (then no sum s_1 + s_2 + s_3 of
+// three shell vectors other than 0 is a multiple of S in any component), or N.
+int shell_grid(int N, int band) {
+    for (int i = 0; i < kNumSizes; ++i)
+        if (kSizes[i] < N && kSizes[i] > 3 * (band - 1)) return kSizes[i];
+    return N;
+}
+
+// Shell fields of one bispectrum shell on grid g: I_a, I_b (, I_c) and,
+// without a cached sum J^3, J, transformed along x (pruned to |ky|, kz < band)
+// and y into out[f] (stride fstride); the z pass follows fused with the sums.
+// a, b, c are half spectra of grid g.
+gridspt_status shell_fields(const Geo& geo, const float2* a, const float2* b, const float2* c, bool has_j,
                             long long lo, long long hi, int band, float2* out, long long fstride, cudaStream_t s) {
-    const double fb = 4.0 * (double)field_floats(p);
-    const double N = p->geo.N, M = p->geo.M;
+    const double N = geo.N, M = geo.M;
+    const double fb = 4.0 * N * N * N;
     const double fx = band > 0 ? (2.0 * band - 1.0) * band / (N * M) : 1.0;   // x columns
     const double fy_in = band > 0 ? (2.0 * band - 1.0) / N * band / M : 1.0;   // y inputs
     const double fy_out = band > 0 ? band / M : 1.0;                         // y outputs
@@ -1403,7 +1436,7 @@ gridspt_status shell_fields(const gridspt_plan_s* p, const float2* a, const floa
         xa.band = band;
         xa.nout = count;
         for (int f = 0; f < count; ++f) xa.codes[f] = x_code(XK_SHELL, 0, srcs[f]);
-        CKP(PK_BX, fb * fx * ((s0 == s1 ? 1 : 2) + count), s, launch_xexp(p->geo, xa, s), "x pass");
+        CKP(PK_BX, fb * fx * ((s0 == s1 ? 1 : 2) + count), s, launch_xexp(geo, xa, s), "x pass");
         return GRIDSPT_OK;
     };
     int nf = 0;
@@ -1426,11 +1459,15 @@ gridspt_status shell_fields(const gridspt_plan_s* p, const float2* a, const floa
     ya.nout = nf;
     ya.band = band;
     for (int f = 0; f < nf; ++f) ya.codes[f] = y_code(f, 0, f);
-    CKP(PK_BY, fb * nf * (fy_in + fy_out), s, launch_yexp(p->geo, ya, s), "y pass");
+    CKP(PK_BY, fb * nf * (fy_in + fy_out), s, launch_yexp(geo, ya, s), "y pass");
     return GRIDSPT_OK;
 }
 
 // E = L^6 sum I_a^2 I_b / sum J^3 (c == NULL) or L^6 sum I_a I_b I_c / sum J^3.
+// Each shell is evaluated on the smallest grid that holds its products
+// without aliasing (shell_grid): the inputs are copied onto that grid once per
+// grid size (the shells come in increasing order) into the workspace's field
+// area, which holds 3 inputs and 4 shell fields of any smaller supported size.
 gridspt_status bispectrum_impl(gridspt_plan p, const void* a_k, const void* b_k, const void* c_k, int32_t nbins,
                                const double* edges, double* e_out, double* ntri_out, void* ws, size_t ws_bytes,
                                gridspt_stream stream) {
@@ -1448,19 +1485,30 @@ gridspt_status bispectrum_impl(gridspt_plan p, const void* a_k, const void* b_k,
     if (!ws || ws_bytes < need) return fail(GRIDSPT_E_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, need);
     if (gridspt_status st = set_device(p)) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long F = field_c(p);
+    const int N = p->geo.N;
     const size_t fb = align256((size_t)field_floats(p) * sizeof(float));
     char* base = static_cast<char*>(ws);
-    float2* fields = reinterpret_cast<float2*>(base);
     double* partial = reinterpret_cast<double*>(base + 4 * fb);
     const double L = p->d.box;
-    const long long fstride = (long long)(fb / sizeof(float2));
     const int G = shell_blocks(p->geo);
     // sum J^3 per shell is data independent: reuse it when the shells match the cached ones
     bool cached = p->j3_nb == nbins;
     for (int i = 0; cached && i <= nbins; ++i) cached = p->j3_thr[i] == bs.thr[i];
     const int triple = c_k ? 1 : 0;
     const int nf = 2 + triple + (cached ? 0 : 1);
+    // distinct inputs (a field passed twice is copied once, so the x pass
+    // still sees equal pointers)
+    const float2* in0[3] = {static_cast<const float2*>(a_k), static_cast<const float2*>(b_k),
+                            static_cast<const float2*>(c_k)};
+    const float2* uniq[3] = {};
+    int slot[3] = {0, 0, 0}, nin = 0;
+    for (int f = 0; f < (c_k ? 3 : 2); ++f) {
+        int j = 0;
+        while (j < nin && uniq[j] != in0[f]) ++j;
+        if (j == nin) uniq[nin++] = in0[f];
+        slot[f] = j;
+    }
+    int have = 0;                       // grid size the workspace's inputs are on (0: none)
     for (int i = 0; i < nbins; ++i) {
         if (bs.thr[i + 1] <= 1) {   // shell holds no mode with k > 0
             CK(cudaMemsetAsync(e_out + i, 0, sizeof(double), s), "bispectrum empty shell");
@@ -1470,15 +1518,36 @@ gridspt_status bispectrum_impl(gridspt_plan p, const void* a_k, const void* b_k,
         }
         // every mode of the shell has |s_a| < band in each component
         const int band = (int)std::floor(std::sqrt((double)(bs.thr[i + 1] - 1))) + 1;
-        if (gridspt_status st = shell_fields(p, static_cast<const float2*>(a_k), static_cast<const float2*>(b_k),
-                                             static_cast<const float2*>(c_k), !cached, bs.thr[i], bs.thr[i + 1], band,
-                                             fields, fstride, s))
+        int S = shell_grid(N, band);
+        const size_t fs = align256((size_t)S * S * S * sizeof(float));
+        if (S < N && (7 * fs > 4 * fb || shell_blocks(sub_geo(p, S)) > G)) S = N;
+        const Geo geo = sub_geo(p, S);
+        const float2* in[3] = {in0[0], in0[1], in0[2]};
+        float2* fields = reinterpret_cast<float2*>(base);
+        long long fstride = (long long)(fb / sizeof(float2));
+        if (S < N) {
+            float2* small = reinterpret_cast<float2*>(base);
+            const long long sstride = (long long)(fs / sizeof(float2));
+            if (S != have) {
+                CKP(PK_BGATHER, 2.0 * nin * (double)S * S * S * 4.0, s,
+                    launch_subgrid(N, S, uniq, nin, small, sstride, s), "bispectrum sub-grid copy");
+                have = S;
+            }
+            for (int f = 0; f < (c_k ? 3 : 2); ++f) in[f] = small + slot[f] * sstride;
+            fields = small + 3 * sstride;
+            fstride = sstride;
+        } else {
+            have = 0;                   // the full-size shell fields overwrite the copies
+        }
+        if (gridspt_status st = shell_fields(geo, in[0], in[1], c_k ? in[2] : nullptr, !cached, bs.thr[i],
+                                             bs.thr[i + 1], band, fields, fstride, s))
             return st;
-        const double fbytes = 4.0 * (double)field_floats(p);
-        CKP(PK_BZ, fbytes * nf * ((double)band / p->geo.M), s,
-            launch_zshell(p->geo, fields, fstride, band, nf, triple, partial, s), "bispectrum z pass and sums");
-        CKP(PK_BISPEC, 16.0 * G, s,
-            launch_bispec_final(p->geo, partial, G, cached ? 2 : 3, p->j3 + i, e_out + i, ntri_out + i,
+        const double fbytes = 4.0 * (double)S * S * S;
+        const int Gs = shell_blocks(geo);
+        CKP(PK_BZ, fbytes * nf * ((double)band / geo.M), s,
+            launch_zshell(geo, fields, fstride, band, nf, triple, partial, s), "bispectrum z pass and sums");
+        CKP(PK_BISPEC, 16.0 * Gs, s,
+            launch_bispec_final(geo, partial, Gs, cached ? 2 : 3, p->j3 + i, e_out + i, ntri_out + i,
                                 L * L * L * L * L * L, s),
             "bispectrum final sum");
     }

@@ -211,8 +211,17 @@ cudaError_t launch_zshell(const Geo& g, const float2* in, long long in_stride, i
                           double* partial, cudaStream_t s);
 cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, int nfields, double* j3_cache,
                                 double* e_out, double* ntri_out, double vol2, cudaStream_t s);
+// Copy the modes of nin half spectra of size N (in[f]) onto a smaller grid of
+// size S (out + f * out_stride, half-spectrum layout of size S): mode s with
+// every component in (-S/2, S/2) keeps its value, the Nyquist planes of the
+// small grid are zero. S <= N, both supported sizes, nin <= 3.
+cudaError_t launch_subgrid(int N, int S, const float2* const* in, int nin, float2* out, long long out_stride,
+                           cudaStream_t s);
 
 bool supported_n(int N);
+// The supported grid sizes in increasing order (kNumSizes of them).
+constexpr int kNumSizes = 15;
+constexpr int kSizes[kNumSizes] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
 
 // emulator network (k_mlp.cu)
 long long mlp_params(int I, int H, int O);

@@ -191,4 +191,49 @@ cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks,
     return cudaGetLastError();
 }
 
+// Sub-grid copy for the bispectrum: every shell field is band limited (each
+// component |s_a| < B), so the sums over cells of a product of three shell
+// fields only see the wavevector sums s_1 + s_2 + s_3 = 0 on any grid of size
+// S > 3 (B - 1) (no other sum is a multiple of S), and the shells can be
+// evaluated on that smaller grid. Two modes (one 16-byte vector) per thread;
+// blockIdx.y selects the field.
+struct SubgridArgs {
+    const float2* in[3];
+    float2* out;
+    long long out_stride;
+    int N, S;
+};
+
+__global__ void __launch_bounds__(256) k_subgrid(SubgridArgs a) {
+    const int S = a.S, MS = S / 2, N = a.N, MN = N / 2;
+    const long long pairs = (long long)S * S * (MS / 2);
+    const long long i2 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i2 >= pairs) return;
+    const long long m0 = 2 * i2;                  // even kz, kz + 1 < S / 2
+    const int kz = (int)(m0 % MS);
+    const long long xy = m0 / MS;
+    const int iy = (int)(xy % S), ix = (int)(xy / S);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ix != S / 2 && iy != S / 2) {
+        const int bx = ix < S / 2 ? ix : ix - S + N;
+        const int by = iy < S / 2 ? iy : iy - S + N;
+        v = __ldg(reinterpret_cast<const float4*>(a.in[blockIdx.y] + ((long long)bx * N + by) * MN + kz));
+    }
+    reinterpret_cast<float4*>(a.out + blockIdx.y * a.out_stride)[i2] = v;
+}
+
+cudaError_t launch_subgrid(int N, int S, const float2* const* in, int nin, float2* out, long long out_stride,
+                           cudaStream_t s) {
+    if (nin < 1 || nin > 3 || S > N || S < 8 || (S / 2) % 2) return cudaErrorInvalidValue;
+    SubgridArgs a{};
+    for (int f = 0; f < nin; ++f) a.in[f] = in[f];
+    a.out = out;
+    a.out_stride = out_stride;
+    a.N = N;
+    a.S = S;
+    const long long pairs = (long long)S * S * (S / 4);
+    k_subgrid<<<dim3((unsigned)((pairs + 255) / 256), (unsigned)nin), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace gridspt

@@ -421,6 +421,34 @@ def test_bispectrum_matches_oracle(N, L, nb):
     assert np.all(np.abs(E[sel] - Er[sel]) <= 1e-4 * np.abs(Er[sel]).max())
 
 
+def test_bispectrum_on_smaller_grids_matches_full_grid_oracle():
+    """Shells whose components stay below B are evaluated on the smallest
+    supported grid S > 3 (B - 1) (inputs copied onto it); at 128^3 with twelve
+    shells up to |s| = 42.4 < N/3 the shells run on grids 12 ... 96 and the last
+    ones on the full grid. E and N_tri against the oracle's full-grid FFT
+    estimator on the same FP32-rounded inputs (two independent Gaussian
+    fields), and the copies onto the smaller grids are seen to run."""
+    N, L, nb = 128, 1000.0, 12
+    kF = 2 * math.pi / L
+    edges = [kF * (0.5 + 41.9 * i / nb) for i in range(nb + 1)]
+    a = spt.linear_field(N, L, 3, COSMO, 41, kcut_lin=kF * 60)
+    b = spt.linear_field(N, L, 3, COSMO, 42, kcut_lin=kF * 60)
+    a = inputs.half_to_full(inputs.full_to_half(a).astype(np.complex64))
+    b = inputs.half_to_full(inputs.full_to_half(b).astype(np.complex64))
+    plan = g.Plan(N, 3, L)
+    g.profile_begin()
+    E, nt = g.bispectrum(plan, to_dev(a), to_dev(b), edges)
+    torch.cuda.synchronize()
+    stats = g.profile_end()
+    assert stats.get("shell_grid", (0,))[0] >= 5          # one copy per distinct smaller grid
+    Er, ntr = estimators.bispectrum_equilateral(a, b, L, edges)
+    assert np.allclose(nt.cpu().numpy(), ntr, rtol=1e-6, atol=1e-3)
+    sel = ntr > 0.5
+    E = E.cpu().numpy()
+    assert sel.all()
+    assert np.all(np.abs(E - Er) <= 1e-4 * np.abs(Er).max())
+
+
 @pytest.mark.parametrize("N,L,nb", [(32, 250.0, 5), (48, 300.0, 6)])
 def test_triple_and_one_loop_bispectrum_match_oracle(N, L, nb):
     """E[a, b, c] for three different fields and the one-loop bispectrum of
