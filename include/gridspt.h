@@ -230,9 +230,13 @@ gridspt_status gridspt_cross_correlation(gridspt_plan plan, const void* a_k, con
  *   edges: HOST double[nbins+1] with edges[nbins] <= 2 k_Ny / 3 (no wrap);
  *   e_out, ntri_out: device double[nbins]; 1 <= nbins <= 64. FP32 fields,
  *   Kahan-compensated FP32 sums over row groups of cells, FP64 across groups,
- *   fixed order. ws: gridspt_bispectrum_workspace_size bytes (4 fields and
- *   the partial sums) of
- *   device scratch. sum_x J^3 does not depend on the data: the first call
+ *   fixed order. Sums over x run on the smallest supported grid S > 3 (B - 1)
+ *   (S <= N) for a shell whose vectors have every component |s_a| < B: there
+ *   the only sum of three shell vectors that is a multiple of S is zero, so
+ *   both sums are those of the N^3 grid times (S/N)^3 and e_out, ntri_out are
+ *   unchanged (the inputs are copied onto that grid in the workspace first).
+ *   ws: gridspt_bispectrum_workspace_size bytes (4 fields of size N and the
+ *   partial sums) of device scratch. sum_x J^3 does not depend on the data: the first call
  *   with a given set of shells computes it and keeps it in the plan (device
  *   memory), later calls with the same shells reuse it, so they must be
  *   ordered after that first call (same stream, or synchronised). */

@@ -559,16 +559,40 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
 // columns; the z pass reads only kz < band. band = floor(sqrt(s2_lin)) + 1
 // bounds every component of an in-band wavevector. The skipped columns hold
 // zeros in the full computation, so the fields are the same.
-void order1_band(const gridspt_plan_s* p, XExpArgs& xa, YZExpArgs& ya, YZExpArgs& za, double* fx, double* fy_in,
-                 double* fy_out) {
-    xa.s2_in = p->s2_lin;
-    const int band = (int)std::floor(std::sqrt((double)p->s2_lin)) + 1;
+void set_band(const gridspt_plan_s* p, int band, XExpArgs& xa, YZExpArgs& ya, YZExpArgs& za, double* fx,
+              double* fy_in, double* fy_out) {
+    band += band & 1;                    // even: the z pass copies rows in kz pairs
     if (band >= p->geo.M) return;
     const double N = p->geo.N, M = p->geo.M;
     xa.band = ya.band = za.band = band;
     *fx = (2.0 * band - 1.0) * band / (N * M);
     *fy_in = (2.0 * band - 1.0) / N * band / M;
     *fy_out = band / M;
+}
+
+void order1_band(const gridspt_plan_s* p, XExpArgs& xa, YZExpArgs& ya, YZExpArgs& za, double* fx, double* fy_in,
+                 double* fy_out) {
+    xa.s2_in = p->s2_lin;
+    set_band(p, (int)std::floor(std::sqrt((double)p->s2_lin)) + 1, xa, ya, za, fx, fy_in, fy_out);
+}
+
+// Band of an order m >= 2 formed in this call (0: none). Every component of
+// an order-1 mode is at most c1 = floor(sqrt(s2_lin)); a product of fields of
+// orders a + b = m then has components at most m c1, and while m c1 < N/2 no
+// product of the recursion up to order m wraps around the grid, so
+// delta_m(k), theta_m(k) vanish at every mode with a component |s_a| > m c1.
+// That holds when every lower order was formed here too (start == 2); stored
+// lower orders are not assumed band limited. With the cut on higher orders
+// (s2_nl >= 0) the finalising pass zeroes every |s|^2 > s2_nl, which bounds
+// the components by floor(sqrt(s2_nl)) whatever the products did.
+int order_band(const gridspt_plan_s* p, int m, int start) {
+    const long long c1 = (long long)std::floor(std::sqrt((double)p->s2_lin));
+    long long c = (start == 2 && 2 * m * c1 < p->geo.N) ? m * c1 : -1;
+    if (p->s2_nl >= 0) {
+        const long long cn = (long long)std::floor(std::sqrt((double)p->s2_nl));
+        c = c < 0 ? cn : std::min(c, cn);
+    }
+    return c < 0 ? 0 : (int)(c + 1);
 }
 
 // Derived fields of order m from its spectra (Sec. II.C steps (2)/(5)),
@@ -616,8 +640,14 @@ gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* 
     const int nin = m == 1 ? 1 : 2;
     double fx = 1.0, fy_in = 1.0, fy_out = 1.0;
     if (m == 1) order1_band(p, xa, ya, za, &fx, &fy_in, &fy_out);
+    else if (fwd) {
+        if (const int band = order_band(p, m, start)) set_band(p, band, xa, ya, za, &fx, &fy_in, &fy_out);
+    }
     CKP(fwd ? PK_XEXP_FWD : PK_XEXP, fb * fx * (fwd ? 2 * nin + xa.nout : nin + xa.nout), s,
         launch_xexp(p->geo, xa, s), "x expansion");
+    if (m >= 2 && xa.band > 0 && fwd)   // the spectra outside the band columns: zeros
+        CKP(PK_XEXP_FWD, fb * 2.0 * (1.0 - fx), s, launch_zero_outside_band(dk, tk, p->geo.N, xa.band, s),
+            "zeros outside the band");
     CKP(PK_YEXP, fb * (fy_in * xa.nout + fy_out * ya.nout), s, launch_yexp(p->geo, ya, s), "y expansion");
     return zexp_pairs(p, m, za, ws, start, spec_delta, s);
 }

@@ -66,7 +66,9 @@ struct XExpArgs {
     long long shell_lo;    // XK_SHELL: 0 < |s|^2, lo <= |s|^2 < hi
     long long shell_hi;
     int band;              // > 0: only columns with |ky| < band and kz < band are
-                           //      transformed and written (all other outputs zero)
+                           //      read, transformed and written; the others are left
+                           //      untouched (their exact values are zero: the
+                           //      caller zeroes them where it needs them)
     long long s2_in = -1;  // backward pass (fwd_first = 0), >= 0: input modes with
                            //      |s|^2 > s2_in are taken as zero (the cut on delta_1)
     // divergence-form sources (fwd_first = 1): when div_in is set, the inputs are
@@ -88,8 +90,8 @@ struct YZExpArgs {
                            // is written to out + slot * out_stride
     int band;              // y pass, > 0: inputs nonzero only at |ky| < band and
                            //      kz < band; only kz < band columns are formed.
-                           // z pass, > 0: inputs nonzero only at kz < band (only
-                           //      those are read); every real output is formed
+                           // z pass, > 0 and even: inputs nonzero only at kz < band
+                           //      (only those are read); every real output is formed
 };
 
 struct IcArgs {
@@ -190,6 +192,9 @@ struct SumOrdersArgs {
     float2* out;
 };
 cudaError_t launch_sum_orders(const SumOrdersArgs& a, cudaStream_t s);
+// Zero the modes of two half spectra of size N outside the band columns
+// (|ky| < band and kz < band, band even, 0 < band < N/2).
+cudaError_t launch_zero_outside_band(float2* f0, float2* f1, int N, int band, cudaStream_t s);
 // r[i] = pab[i] / sqrt(paa[i] pbb[i]) (0 where the denominator vanishes), nbins <= 64
 cudaError_t launch_rcorr(const double* pab, const double* paa, const double* pbb, int nbins, double* r,
                          cudaStream_t s);

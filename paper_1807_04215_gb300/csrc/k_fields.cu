@@ -8,6 +8,7 @@
 // * the cross-correlation coefficient r = P_ab / sqrt(P_aa P_bb) per bin
 //   (Eqs. r_corr_nthPT, r_corr_sum_nth) from three shell power spectra (the
 //   volume and N_k factors cancel), FP64.
+// * zeros outside the band columns of band-limited spectra (run_orders).
 #include "gridspt_internal.h"
 
 namespace gridspt {
@@ -45,6 +46,22 @@ __global__ void __launch_bounds__(256) k_sum_orders(SumOrdersArgs a) {
     reinterpret_cast<float4*>(a.out)[i2] = acc;
 }
 
+// Spectra of order n >= 2 formed from band-limited lower orders are zero
+// outside the band columns; the x pass that finalises them moves only those
+// columns, and this kernel writes the zeros of the others. One 16-byte vector
+// (two kz modes) per thread, blockIdx.y selects the field.
+__global__ void __launch_bounds__(256) k_zero_outside_band(float2* f0, float2* f1, int N, int band) {
+    const int M = N / 2;
+    const long long pairs = (long long)N * N * (M / 2);
+    const long long i2 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i2 >= pairs) return;
+    const long long m0 = 2 * i2;
+    const int kz = (int)(m0 % M);                  // even: the pair lies on one side of the even band edge
+    const int ky = (int)((m0 / M) % N);
+    if (kz < band && (ky < band || ky > N - band)) return;
+    reinterpret_cast<float4*>(blockIdx.y ? f1 : f0)[i2] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void k_rcorr(const double* __restrict__ pab, const double* __restrict__ paa,
                         const double* __restrict__ pbb, int nbins, double* __restrict__ r) {
     const int i = threadIdx.x;
@@ -58,6 +75,13 @@ __global__ void k_rcorr(const double* __restrict__ pab, const double* __restrict
 cudaError_t launch_sum_orders(const SumOrdersArgs& a, cudaStream_t s) {
     const long long pairs = (long long)a.N * a.N * (a.N / 2) / 2;
     k_sum_orders<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_outside_band(float2* f0, float2* f1, int N, int band, cudaStream_t s) {
+    if (band <= 0 || (band & 1) || 2 * band >= N) return cudaErrorInvalidValue;
+    const long long pairs = (long long)N * N * (N / 4);
+    k_zero_outside_band<<<dim3((unsigned)((pairs + 255) / 256), 2), 256, 0, s>>>(f0, f1, N, band);
     return cudaGetLastError();
 }
 

@@ -94,9 +94,11 @@ __device__ __forceinline__ void tile_prefetch(float2* tile, const float2* src, l
 // Copy TZ contiguous rows of M float2 between global memory and a shared tile
 // of odd pitch PITCH. Consecutive threads move consecutive float2 of a row
 // (coalesced, conflict-free); all loads are issued before the shared stores,
-// so each thread has TZ * M / NTHR requests in flight.
+// so each thread has TZ * M / NTHR requests in flight. band > 0: only the
+// first band entries of each row are read, the rest of the tile row is zero.
 template <int M, int TZ, int PITCH, int NTHR>
-__device__ __forceinline__ void tile_load(float2* tile, const float2* src, long long row0, long long rows) {
+__device__ __forceinline__ void tile_load(float2* tile, const float2* src, long long row0, long long rows,
+                                          int band = 0) {
     constexpr int NV = TZ * M;
     constexpr int PER = (NV + NTHR - 1) / NTHR;
     float2 v[PER];
@@ -105,7 +107,7 @@ __device__ __forceinline__ void tile_load(float2* tile, const float2* src, long 
         const int idx = threadIdx.x + u * NTHR;
         const int r = idx / M, j = idx - r * M;
         const long long row = row0 + r;
-        v[u] = (idx < NV && row < rows) ? src[row * M + j] : make_float2(0.f, 0.f);
+        v[u] = (idx < NV && row < rows && (band <= 0 || j < band)) ? src[row * M + j] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
@@ -593,7 +595,9 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     const long long rows = (long long)N * N;
     const long long row0 = (long long)blockIdx.x * TZ;
     const YZExpArgs& z = args.z;
-    constexpr int B = 0;                         // pair launches never have a band
+    // z.band > 0: the inputs are nonzero only at kz < band; the input tile is
+    // loaded zero-filled beyond it, so the transform needs no per-element test
+    constexpr int B = 0;
     // real fields as rows of M float2 (cells 2k, 2k + 1)
     const long long fstride2 = args.cells / 2;
     float2 accA[NT][E], accB[NT][E];
@@ -618,7 +622,7 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                                                  row0, rows);
         }
         if (in != cur) {
-            tile_load<M, TZ, PITCH, NTH>(tin, z.in + in * z.in_stride, row0, rows);
+            tile_load<M, TZ, PITCH, NTH>(tin, z.in + in * z.in_stride, row0, rows, z.band);
             __syncthreads();
             cur = in;
         }
@@ -752,6 +756,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+// The same copy, or (read = false) 16 zero bytes written without reading src.
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool read) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(read ? 16 : 0)
+                 : "memory");
+}
 
 // Lane-major twiddle tables of a warp-row kernel from the global table of
 // N-th roots (values identical to the tile kernels' shared copy).
@@ -766,7 +776,7 @@ __device__ __forceinline__ void zrow_tables(float2* twl, float2* twp, const floa
     __syncthreads();
 }
 
-template <int N, int NT>
+template <int N, int NT, bool BAND>
 __global__ void __launch_bounds__(kRowWarps * 32, 2)
 k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     using C = RowCfg<N>;
@@ -783,9 +793,15 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     float2* wpt = wbase + 2 * WIN;                                                 // [MAXP][RW][M] partners
     float2* xrow = wbase + WIN * (NT ? 2 + C::MAXP : 2) + r * C::XROW;              // this row's exchange buffer
     const YZExpArgs& z = args.z;
-    // > 0: inputs nonzero only at kz < B (only those are loaded); only the
-    // store-only launch of order 1 has a band, the pair forms fold it away
-    const int B = NT == 0 ? z.band : 0;
+    // BAND, z.band > 0 (even): inputs nonzero only at kz < B. Only those are
+    // read; the rest of the input buffers is zero-filled by the copies, so the
+    // transform needs no per-element test (a separate instance, which keeps
+    // the mask's registers out of the launches without a band)
+    const int B = BAND ? z.band : 0;
+    unsigned inb = 0;            // bit u: this lane's 16-byte piece u of a row window lies at kz < B
+#pragma unroll
+    for (int u = 0; u < WIN / 64; ++u)
+        if (B <= 0 || (2 * (lane + 32 * u)) % M < B) inb |= 1u << u;
     const long long rows = (long long)N * N;
     const long long groups = rows / RW;
     const long long gstride = (long long)gridDim.x * kRowWarps;
@@ -827,11 +843,9 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                     float4 v[WIN / 64];
 #pragma unroll
                     for (int u = 0; u < WIN / 64; ++u)
-                        if (B <= 0 || (2 * (lane + 32 * u)) % M < B) v[u] = __ldg(src + lane + 32 * u);
+                        v[u] = ((inb >> u) & 1u) ? __ldg(src + lane + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int u = 0; u < WIN / 64; ++u)
-                        if (B <= 0 || (2 * (lane + 32 * u)) % M < B)
-                            reinterpret_cast<float4*>(wbase + buf * WIN)[lane + 32 * u] = v[u];
+                    for (int u = 0; u < WIN / 64; ++u) reinterpret_cast<float4*>(wbase + buf * WIN)[lane + 32 * u] = v[u];
                     __syncwarp();
                 }
                 cur = in;
@@ -846,8 +860,7 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                     float2* dst = wbase + (buf ^ 1) * WIN;
 #pragma unroll
                     for (int u = 0; u < WIN / 64; ++u)
-                        if (B <= 0 || (2 * (lane + 32 * u)) % M < B)
-                            cp_async16(dst + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
+                        cp_async16z(dst + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u), (inb >> u) & 1u);
                     have_next = true;
                 }
             }
@@ -857,8 +870,8 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int k = p + P * i;
-                float2 Xk = (B <= 0 || k < B) ? colp[k] : make_float2(0.f, 0.f);
-                float2 Xm = (k && (B <= 0 || M - k < B)) ? colp[M - k] : make_float2(0.f, 0.f);
+                float2 Xk = colp[k];
+                float2 Xm = k ? colp[M - k] : make_float2(0.f, 0.f);
                 if (g) {
                     const float k1 = kF * (float)k, k2 = kF * (float)(M - k);
                     Xk = cscale(Xk, g == 1 ? k1 : k1 * k1);
@@ -1447,23 +1460,27 @@ struct Launch {
     // warp-row z pass (store only for NT = 0); persistent grid of resident blocks
     template <int NT>
     static cudaError_t zrow(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
+        return a.z.band > 0 ? zrow_k<NT, true>(g, a, s) : zrow_k<NT, false>(g, a, s);
+    }
+    template <int NT, bool BAND>
+    static cudaError_t zrow_k(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
         using C = RowCfg<N>;
         if constexpr (!C::ok) {
             return cudaErrorNotSupported;
         } else {
             const size_t smem = C::smem(NT);
-            cudaError_t e = set_smem(k_zrow<N, NT>, smem);
+            cudaError_t e = set_smem(k_zrow<N, NT, BAND>, smem);
             if (e != cudaSuccess) return e;
             int dev = 0, sms = 0, per = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow<N, NT>, kRowWarps * 32, smem)) !=
-                cudaSuccess)
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zrow<N, NT, BAND>, kRowWarps * 32,
+                                                                     smem)) != cudaSuccess)
                 return e;
             const long long groups = (long long)N * N / C::RW;
             const long long need = (groups + kRowWarps - 1) / kRowWarps;
             const long long resident = (long long)(per > 0 ? per : 1) * sms;
-            k_zrow<N, NT><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
+            k_zrow<N, NT, BAND><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
                 a, g.tw, (float)g.kF);
             return cudaGetLastError();
         }
@@ -1547,6 +1564,7 @@ struct Launch {
                       : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template yexp<false>(g, a, s);              \
     }                                                                                                      \
     cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
+        if (a.band & 1) return cudaErrorInvalidValue; /* row copies move kz pairs */                       \
         if (v == 2 && RowCfg<N>::ok) {                                                                    \
             ZPairArgs za{};                                                                                \
             za.z = a;                                                                                      \
@@ -1557,6 +1575,7 @@ struct Launch {
     }                                                                                                      \
     int transform_shell_blocks_##N() { return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::shell_blocks(); }     \
     cudaError_t transform_zexp_pairs_##N(const Geo& g, const ZPairArgs& a, cudaStream_t s) {               \
+        if (a.z.band & 1) return cudaErrorInvalidValue; /* row copies move kz pairs */                     \
         if (g.var[TV_ZEXP] == 2 && RowCfg<N>::ok)                                                          \
             return a.ntargets <= 1 ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zrow<1>(g, a, s)        \
                                    : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template zrow<2>(g, a, s);       \

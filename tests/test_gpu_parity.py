@@ -265,6 +265,35 @@ def test_modes_of_delta1_above_the_cut_are_ignored():
     assert torch.equal(g.run_orders(plan, dirty), ref)
 
 
+def test_order_two_spectra_vanish_outside_their_band():
+    """delta_2, theta_2 are products of two order-1 fields whose components are
+    at most c1 = floor(sqrt(s2_lin)); with 4 c1 < N no product wraps, so every
+    mode with |s_y| or s_z above 2 c1 is zero. The oracle's full computation is
+    zero there to FP64 rounding; the GPU forms only the band columns (|ky|,
+    kz < B, B = 2 c1 + 2 rounded to even) and writes exact zeros elsewhere."""
+    N, L, n_max = 64, 500.0, 5
+    plan = g.Plan(N, n_max, L)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, 5)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    sp = g.run_orders(plan, to_dev(ref1)[None])
+    r = N / (n_max + 1)
+    c1 = math.isqrt(math.floor(r * r))
+    B = 2 * c1 + 1
+    B += B & 1
+    assert 4 * c1 < N and B < N // 2
+    sy = np.fft.fftfreq(N, 1.0 / N).astype(int)[None, :, None]
+    kz = np.arange(N // 2)[None, None, :]
+    out = (np.abs(sy) >= B) | (kz >= B)
+    out = np.broadcast_to(out, (N, N, N // 2))
+    dk, tk = spt.run_orders(ref1, L, 2)
+    for which, ref in ((0, dk[2]), (1, tk[2])):
+        half = ref[:, :, : N // 2]
+        assert np.abs(half[out]).max() <= 1e-12 * np.abs(half).max()       # the exact values
+        got = host(sp[0, 0, which])
+        assert np.all(got[out] == 0)
+        assert rms_rel(got, ref) < 1e-5
+
+
 def test_resume_equals_full_run_bitwise():
     N, L, n_max = 64, 400.0, 5
     plan = g.Plan(N, n_max, L)
