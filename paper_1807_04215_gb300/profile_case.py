@@ -9,8 +9,11 @@ CASE is one of:
   power    the six P-terms of one realisation (32 log bins, 0.01-0.4 h/Mpc)
   bispec   the equilateral bispectrum of one realisation (16 shells)
 Each case runs `reps` times (default 2) so that a profiler can skip the first.
+--stats prints the library's per-kind launches, event time and algorithmic
+bytes of the last repetition (JSON).
 """
 import argparse
+import json
 import math
 
 import torch
@@ -25,6 +28,7 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--nmax", type=int, default=5)
     ap.add_argument("--tuning", default="", help="tile variants per pass, e.g. 0,0,1,0,0")
+    ap.add_argument("--stats", action="store_true", help="print per-kind stats of the last repetition")
     a = ap.parse_args()
     N = a.n
     L = 2000.0 * N / 512
@@ -47,7 +51,10 @@ def main():
         edges = [0.01 * 40.0 ** (i / 32) for i in range(33)]
         kc = 2 * math.pi / L * N / (n_max + 1)
         bedges = [kc * i / 16 for i in range(17)]
-        for _ in range(a.reps):
+        for rep in range(a.reps):
+            if a.stats and rep == a.reps - 1:
+                torch.cuda.synchronize()
+                g.profile_begin()
             if a.case == "orders":
                 g.make_linear_field(plan, [1000], out=d1)
                 spectra = g.run_orders(plan, d1)
@@ -59,6 +66,9 @@ def main():
             else:
                 g.bispectrum(plan, d1[0], spectra[0, 0, 0], bedges)
     torch.cuda.synchronize()
+    if a.stats and a.case not in ("c2r", "r2c"):
+        st = g.profile_end()
+        print(json.dumps({k: {"launches": v[0], "ms": round(v[1], 4), "GB": round(v[2] / 1e9, 4)} for k, v in st.items()}))
     print("ok", a.case, N)
 
 
