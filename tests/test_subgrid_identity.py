@@ -1,0 +1,57 @@
+"""The identity behind the library's smaller-grid bispectrum (CPU, FP64).
+
+Every vector of a shell whose components satisfy |s_a| < B can be stored on a
+grid of size S; the sum over the S^3 cells of a product of three shell fields
+keeps the triangles s_1 + s_2 + s_3 = 0 (mod S in each component). When
+S > 3 (B - 1) no other sum is a multiple of S, so the sums are those of the
+N^3 grid times (S/N)^3 and E, N_tri are unchanged; at S = 3 (B - 1) wrapped
+triangles enter. Checked with the oracle's FFT shell estimator on both grids.
+"""
+import math
+
+import numpy as np
+
+from oracle import estimators
+from tests import inputs
+
+
+def _on_grid(a, S):
+    """The modes of a full N^3 spectrum with every component in (-S/2, S/2),
+    placed on an S^3 grid (Nyquist planes of the small grid zero)."""
+    N = a.shape[0]
+    s = np.fft.fftfreq(S, 1.0 / S).astype(int)
+    idx = s % N
+    out = a[np.ix_(idx, idx, idx)].copy()
+    out[S // 2, :, :] = 0
+    out[:, S // 2, :] = 0
+    out[:, :, S // 2] = 0
+    return out
+
+
+def test_shell_sums_on_smaller_grids_equal_the_full_grid():
+    N, L = 48, 300.0
+    kF = 2 * math.pi / L
+    a = np.fft.fftn(inputs.random_real((N, N, N), 1))
+    b = np.fft.fftn(inputs.random_real((N, N, N), 2))
+    # shells [lo, hi) in units of k_F; B - 1 = largest component, grid = smallest supported S > 3 (B - 1)
+    for lo, hi, S in [(0.5, 4.0, 12), (4.0, 7.0, 24), (7.0, 10.0, 32)]:
+        edges = [kF * lo, kF * hi]
+        E, nt = estimators.bispectrum_equilateral(a, b, L, edges)
+        Es, nts = estimators.bispectrum_equilateral(_on_grid(a, S), _on_grid(b, S), L, edges)
+        assert nt[0] > 0.5
+        assert abs(nts[0] - nt[0]) <= 1e-9 * nt[0]
+        assert abs(Es[0] - E[0]) <= 1e-10 * abs(E[0])
+
+
+def test_a_grid_of_three_times_the_band_wraps_triangles_in():
+    """Shell 3.5 <= |s| < 4.5 holds s = (4, 0, 0): B - 1 = 4, so S = 12 = 3 (B - 1)
+    also counts the wrapped triangles (4, 0, 0) x 3 = (12, 0, 0); S = 16 does not."""
+    N, L = 48, 300.0
+    kF = 2 * math.pi / L
+    a = np.fft.fftn(inputs.random_real((N, N, N), 3))
+    edges = [kF * 3.5, kF * 4.5]
+    E, nt = estimators.bispectrum_equilateral(a, a, L, edges)
+    _, nt16 = estimators.bispectrum_equilateral(_on_grid(a, 16), _on_grid(a, 16), L, edges)
+    _, nt12 = estimators.bispectrum_equilateral(_on_grid(a, 12), _on_grid(a, 12), L, edges)
+    assert abs(nt16[0] - nt[0]) <= 1e-9 * nt[0]
+    assert nt12[0] > nt[0] + 0.5
