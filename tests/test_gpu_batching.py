@@ -72,6 +72,35 @@ def test_tile_variants_give_identical_results(N, n_max):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("N", [64, 256])
+def test_variants_identical_with_the_higher_order_cut(N):
+    """With k_cut,2 every order m >= 2 has the band of that cut: the x and y
+    passes move only band columns and every z launch (store-only, one target,
+    two targets) reads only kz < band, zero-filling its row buffers in the
+    warp-row form and its tiles in the tile form. All variants agree bit for
+    bit, and the spectra vanish outside the band columns."""
+    L = 4.0 * N
+    kF = 2 * np.pi / L
+    kc = kF * N / 6
+    plan = g.Plan(N, 5, L, kcut_lin=kc, kcut_nl=4.0 / 3.0 * kc)
+    d1 = g.make_linear_field(plan, [6])
+    results = []
+    for choice in ([0] * 5, [1, 1, 1, 1, 1], [1, 1, 3, 2, 2], [1, 1, 4, 2, 2]):
+        g.set_tuning(plan, choice)
+        results.append(g.run_orders(plan, d1).clone())
+        g.check(plan)
+    for r in results[1:]:
+        assert torch.equal(results[0], r)
+    B = int(np.floor(np.sqrt(np.floor((4.0 / 3.0 * N / 6) ** 2)))) + 1
+    B += B & 1
+    sy = torch.from_numpy(np.fft.fftfreq(N, 1.0 / N).astype(np.int64)).cuda()
+    outside = (sy.abs() >= B)[None, :, None] | (torch.arange(N // 2, device="cuda") >= B)[None, None, :]
+    for m in range(2, 6):
+        for w in range(2):
+            assert torch.all(results[0][0, m - 2, w][outside.expand(N, N, N // 2)] == 0)
+    del results
+
+
 @pytest.mark.parametrize("N", [32, 64, 256])
 def test_bispectrum_identical_for_warp_row_z_pass(N):
     """The bispectrum's z pass in warp-row form (z expansion variant 2) forms
