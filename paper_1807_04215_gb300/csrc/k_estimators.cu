@@ -7,10 +7,11 @@
 // integer ranges of |s|^2 precomputed on the host from the FP64 edges, so
 // the bin decision equals the FP64 test edges[i] <= k_F sqrt(|s|^2).
 //
-// Determinism: one warp per (kx, ky) row, 32 consecutive kz per step. Along a
-// row the bin index is non-decreasing in kz, so lanes with equal bins are
-// contiguous: a segmented shuffle scan sums each run and its last lane adds
-// the run to the warp's FP64 accumulator (one writer per bin per step). Warps
+// Determinism: one warp per (kx, ky) row, chunks of 32 consecutive kz (two
+// chunks per step, scanned side by side). Along a row the bin index is
+// non-decreasing in kz, so lanes with equal bins are contiguous: a segmented
+// shuffle scan sums each run and its last lane adds the run to the warp's FP64
+// accumulator (one writer per bin per chunk, chunks in kz order). Warps
 // and blocks are then summed in a fixed order: results are bitwise repeatable.
 // The scan runs in FP32 with each addition's rounding error carried exactly
 // (Knuth's two-sum) and added at the tail, so a run's sum is good to about
@@ -52,53 +53,67 @@ k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins
         if (sxy >= top) continue;
         const float2* ar = a + row * M;
         const float2* br = b + row * M;
-        for (int kz0 = 0; kz0 < M; kz0 += 32) {
+        // two chunks of 32 kz per step: their scans are independent chains
+        // (latency hiding); their sums reach acc in chunk order, as one at a time
+        for (int kz0 = 0; kz0 < M; kz0 += 64) {
             if (sxy + kz0 * kz0 >= top) break;
-            const int kz = kz0 + lane;
-            const int s2 = sxy + kz * kz;
-            int bin;
-            if (kz >= M || s2 >= top) {
-                bin = nb;                       // above every bin
-            } else if (s2 == 0 || s2 < thr[0]) {
-                bin = -1;                       // k = 0 or below the first edge
-            } else {
-                int lo = 0, hi = nb;            // thr[lo] <= s2 < thr[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (thr[mid] <= s2) lo = mid; else hi = mid;
+            float v[2], e[2], c[2];              // sum, carried rounding error, weight
+            int bin[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kz = kz0 + 32 * h + lane;
+                const int s2 = sxy + kz * kz;
+                if (kz >= M || s2 >= top) {
+                    bin[h] = nb;                 // above every bin
+                } else if (s2 == 0 || s2 < thr[0]) {
+                    bin[h] = -1;                 // k = 0 or below the first edge
+                } else {
+                    int lo = 0, hi = nb;         // thr[lo] <= s2 < thr[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (thr[mid] <= s2) lo = mid; else hi = mid;
+                    }
+                    bin[h] = lo;
                 }
-                bin = lo;
+                v[h] = 0.f;
+                e[h] = 0.f;
+                c[h] = 0.f;
+                if (bin[h] >= 0 && bin[h] < nb) {
+                    const float2 x = ar[kz], y = br[kz];
+                    const float wgt = kz == 0 ? 1.f : 2.f;
+                    v[h] = wgt * fmaf(x.x, y.x, x.y * y.y);
+                    c[h] = wgt;
+                }
             }
-            float v = 0.f, e = 0.f, c = 0.f;     // sum, carried rounding error, weight
-            if (bin >= 0 && bin < nb) {
-                const float2 x = ar[kz], y = br[kz];
-                const float wgt = kz == 0 ? 1.f : 2.f;
-                v = wgt * fmaf(x.x, y.x, x.y * y.y);
-                c = wgt;
-            }
-            // segmented inclusive scan over runs of equal bin
+            // segmented inclusive scans over runs of equal bin
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const float ov = __shfl_up_sync(0xffffffffu, v, off);
-                const float oe = __shfl_up_sync(0xffffffffu, e, off);
-                const float oc = __shfl_up_sync(0xffffffffu, c, off);
-                const int ob = __shfl_up_sync(0xffffffffu, bin, off);
-                if (lane >= off && ob == bin) {
-                    const float t = __fadd_rn(v, ov);            // two-sum: t + r = v + ov exactly
-                    const float bv = __fsub_rn(t, v);
-                    const float r = __fadd_rn(__fsub_rn(v, __fsub_rn(t, bv)), __fsub_rn(ov, bv));
-                    v = t;
-                    e = __fadd_rn(__fadd_rn(e, oe), r);
-                    c += oc;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float ov = __shfl_up_sync(0xffffffffu, v[h], off);
+                    const float oe = __shfl_up_sync(0xffffffffu, e[h], off);
+                    const float oc = __shfl_up_sync(0xffffffffu, c[h], off);
+                    const int ob = __shfl_up_sync(0xffffffffu, bin[h], off);
+                    if (lane >= off && ob == bin[h]) {
+                        const float t = __fadd_rn(v[h], ov);         // two-sum: t + r = v + ov exactly
+                        const float bv = __fsub_rn(t, v[h]);
+                        const float r = __fadd_rn(__fsub_rn(v[h], __fsub_rn(t, bv)), __fsub_rn(ov, bv));
+                        v[h] = t;
+                        e[h] = __fadd_rn(__fadd_rn(e[h], oe), r);
+                        c[h] += oc;
+                    }
                 }
             }
-            const int nxt = __shfl_down_sync(0xffffffffu, bin, 1);
-            const bool tail = (lane == 31) || (nxt != bin);
-            if (tail && bin >= 0 && bin < nb) {
-                acc[w][bin] += (double)v + (double)e;
-                acc[w][kMaxBins + bin] += (double)c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int nxt = __shfl_down_sync(0xffffffffu, bin[h], 1);
+                const bool tail = (lane == 31) || (nxt != bin[h]);
+                if (tail && bin[h] >= 0 && bin[h] < nb) {
+                    acc[w][bin[h]] += (double)v[h] + (double)e[h];
+                    acc[w][kMaxBins + bin[h]] += (double)c[h];
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
     __syncthreads();
