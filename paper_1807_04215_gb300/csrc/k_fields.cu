@@ -51,13 +51,13 @@ __global__ void __launch_bounds__(256) k_sum_orders(SumOrdersArgs a) {
 // columns, and this kernel writes the zeros of the others. One 16-byte vector
 // (two kz modes) per thread, blockIdx.y selects the field.
 __global__ void __launch_bounds__(256) k_zero_outside_band(float2* f0, float2* f1, int N, int band) {
-    const int M = N / 2;
-    const long long pairs = (long long)N * N * (M / 2);
-    const long long i2 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int H = N / 4;                           // 16-byte pairs per row
+    const int pairs = N * N * H;                   // < 2^31 for N <= 1024
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (i2 >= pairs) return;
-    const long long m0 = 2 * i2;
-    const int kz = (int)(m0 % M);                  // even: the pair lies on one side of the even band edge
-    const int ky = (int)((m0 / M) % N);
+    const int row = i2 / H;
+    const int kz = 2 * (i2 - row * H);             // even: the pair lies on one side of the even band edge
+    const int ky = row % N;
     if (kz < band && (ky < band || ky > N - band)) return;
     reinterpret_cast<float4*>(blockIdx.y ? f1 : f0)[i2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }

@@ -786,7 +786,7 @@ __device__ __forceinline__ void zrow_tables(float2* twl, float2* twp, const floa
 }
 
 template <int N, int NT, bool BAND>
-__global__ void __launch_bounds__(kRowWarps * 32, 2)
+__global__ void __launch_bounds__(kRowWarps * 32, NT == 0 ? 3 : 2)
 k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
     using C = RowCfg<N>;
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW, WIN = C::WIN;
@@ -1269,7 +1269,7 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
 }
 
 template <int N>
-__global__ void __launch_bounds__(kRowWarps * 32, 2)
+__global__ void __launch_bounds__(kRowWarps * 32, 3)
 k_zrow_r2c(const float2* in, float2* out, long long fstride, int count, const float2* __restrict__ twg,
            float scale) {
     using C = RowCfg<N>;
