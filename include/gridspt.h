@@ -132,7 +132,14 @@ gridspt_status gridspt_make_linear_field(gridspt_plan plan, const gridspt_cosmo*
  *             only the columns inside that cut.
  *   spectra:  device float2[batch][n_max-1][2][N][N][N/2]; slot [b][n-2][0] is
  *             delta_n(k), [b][n-2][1] is theta_n(k), n = 2..n_max (written for
- *             n >= start_order, read for 2 <= n < start_order).
+ *             n >= start_order, read for 2 <= n < start_order). An order n
+ *             formed in the call whose modes have every component at most c_n
+ *             (c_n = n floor(sqrt(s2_lin)) while 2 c_n < N and all lower orders
+ *             were formed in the same call; with kcut_nl at most
+ *             floor(sqrt(s2_nl))) is transformed only on the columns
+ *             |ky|, kz < B, B = c_n + 1 rounded up to even, when B < N/2, and
+ *             is written as exact zeros outside them, where its exact values
+ *             vanish. s2_lin = floor((kcut_lin / k_F)^2), likewise s2_nl.
  *   start_order: 2 for a full run; 3..n_max resumes from stored lower orders
  *             (Sec. II.C: only delta_m, theta_m are needed to continue).
  *   ws, ws_bytes: device scratch of at least gridspt_workspace_size bytes.

@@ -1424,14 +1424,18 @@ namespace {
 
 // Geometry of the grid of size S <= N that shares the plan's box (same k_F,
 // tile variants and status word) for the band-limited bispectrum shells.
-Geo sub_geo(const gridspt_plan_s* p, int S) {
-    Geo g = p->geo;
-    if (S == p->geo.N) return g;
-    for (int i = 0; i < kNumSizes; ++i)
-        if (kSizes[i] == S && p->sub_off[i] >= 0) g.tw = p->tw + p->sub_off[i];
-    g.N = S;
-    g.M = S / 2;
-    return g;
+bool sub_geo(const gridspt_plan_s* p, int S, Geo* out) {
+    *out = p->geo;
+    if (S == p->geo.N) return true;
+    for (int i = 0; i < kNumSizes; ++i) {
+        if (kSizes[i] == S && p->sub_off[i] >= 0) {
+            out->tw = p->tw + p->sub_off[i];
+            out->N = S;
+            out->M = S / 2;
+            return true;
+        }
+    }
+    return false;                       // no table of that size in the plan
 }
 
 // Grid on which a shell with every component |s_a| < band is evaluated: the
@@ -1549,9 +1553,13 @@ gridspt_status bispectrum_impl(gridspt_plan p, const void* a_k, const void* b_k,
         // every mode of the shell has |s_a| < band in each component
         const int band = (int)std::floor(std::sqrt((double)(bs.thr[i + 1] - 1))) + 1;
         int S = shell_grid(N, band);
+        Geo geo{};
+        if (!sub_geo(p, S, &geo)) return fail(GRIDSPT_E_INVALID, "internal: no transform table for grid %d", S);
         const size_t fs = align256((size_t)S * S * S * sizeof(float));
-        if (S < N && (7 * fs > 4 * fb || shell_blocks(sub_geo(p, S)) > G)) S = N;
-        const Geo geo = sub_geo(p, S);
+        if (S < N && (7 * fs > 4 * fb || shell_blocks(geo) > G)) {
+            S = N;
+            sub_geo(p, S, &geo);
+        }
         const float2* in[3] = {in0[0], in0[1], in0[2]};
         float2* fields = reinterpret_cast<float2*>(base);
         long long fstride = (long long)(fb / sizeof(float2));
