@@ -47,7 +47,7 @@ extern "C" {
 typedef enum {
     GRIDSPT_OK = 0,
     GRIDSPT_E_INVALID = 1,     /* bad argument, size, alignment or workspace */
-    GRIDSPT_E_UNSUPPORTED = 2, /* valid request outside what this build supports */
+    GRIDSPT_E_UNSUPPORTED = 2, /* valid request outside what the library supports */
     GRIDSPT_E_NOMEM = 3,       /* plan tables could not be allocated */
     GRIDSPT_E_CUDA = 4,        /* a CUDA runtime call or launch failed */
     GRIDSPT_E_TIMEOUT = 5,     /* reserved: a bounded device-side wait gave up */

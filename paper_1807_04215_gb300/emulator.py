@@ -3,8 +3,8 @@
 Maps the linear-spectrum parameters (sigma_8, n_s, Gamma) to the loop terms
 P22, P13, P33, P24, P15 in log k-bins, with a 3 -> 128 -> 128 -> (5 x bins)
 SiLU network whose forward, backward, loss and Adam kernels are the library's
-own (gridspt_mlp_*). Training targets are made by GridSPT itself; GridSPT is
-also the judge of the emulator's error and the fallback outside the box it
+own (gridspt_mlp_*). Training targets are made by GridSPT itself; GridSPT
+also measures the emulator's error and is the fallback outside the box it
 was trained on.
 
 Target scaling: with the seeds held fixed, every delta_n is proportional to

@@ -1,6 +1,6 @@
 """P-term emulator end to end on a small workload: GridSPT (64^3, L = 250
 Mpc/h, n_max = 5, 2 seeds) makes the training set on a Latin hypercube, the
-network is trained with the library's kernels, and GridSPT judges it on
+network is trained with the library's kernels, and GridSPT measures its error on
 held-out points and serves as the fallback outside the training box. Also
 measures what the network gains: cosmologies per second vs. the grid method
 on the same GPU."""
