@@ -1,4 +1,6 @@
-"""The identity behind the library's smaller-grid bispectrum (CPU, FP64).
+"""Identities behind the work the library skips (CPU, FP64, on the oracle).
+
+Smaller-grid bispectrum:
 
 Every vector of a shell whose components satisfy |s_a| < B can be stored on a
 grid of size S; the sum over the S^3 cells of a product of three shell fields
@@ -6,6 +8,10 @@ keeps the triangles s_1 + s_2 + s_3 = 0 (mod S in each component). When
 S > 3 (B - 1) no other sum is a multiple of S, so the sums are those of the
 N^3 grid times (S/N)^3 and E, N_tri are unchanged; at S = 3 (B - 1) wrapped
 triangles enter. Checked with the oracle's FFT shell estimator on both grids.
+
+Band-limited orders: products of fields whose modes have components at most
+a c1 and b c1 have components at most (a + b) c1; while that stays below N/2
+nothing wraps, so the higher orders vanish outside their band.
 """
 import math
 
@@ -55,3 +61,27 @@ def test_a_grid_of_three_times_the_band_wraps_triangles_in():
     _, nt12 = estimators.bispectrum_equilateral(_on_grid(a, 12), _on_grid(a, 12), L, edges)
     assert abs(nt16[0] - nt[0]) <= 1e-9 * nt[0]
     assert nt12[0] > nt[0] + 0.5
+
+
+def test_orders_formed_from_a_band_limited_field_vanish_outside_their_band():
+    """The identity behind the library's band-limited passes of orders m >= 2:
+    with every component of delta_1's modes at most c1, delta_m and theta_m
+    vanish at every mode with a component above m c1 as long as m c1 < N/2 (no
+    product of the recursion up to order m wraps around the grid). The
+    oracle's FP64 recursion on 32^3, with the default cut N/6 (c1 = 5: orders 2
+    and 3 have a band inside the grid) and with a linear cut at 3.5 k_F (c1 = 3:
+    every order up to 5)."""
+    from oracle import cosmology, spt
+    N, L, n_max = 32, 250.0, 5
+    kF = 2 * math.pi / L
+    s = np.abs(np.fft.fftfreq(N, 1.0 / N).astype(int))
+    comp = np.maximum(np.maximum(s[:, None, None], s[None, :, None]), s[None, None, :])
+    for kcut, c1, banded in [(None, 5, (2, 3)), (3.5 * kF, 3, (2, 3, 4, 5))]:
+        d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, 3, kcut_lin=kcut)
+        dk, tk = spt.run_orders(d1, L, n_max)
+        for m in banded:
+            assert 2 * m * c1 < N
+            outside = comp > m * c1
+            assert outside.sum() > 0
+            for f in (dk[m], tk[m]):
+                assert np.abs(f[outside]).max() <= 1e-12 * np.abs(f).max(), (kcut, m)
