@@ -294,6 +294,28 @@ def test_order_two_spectra_vanish_outside_their_band():
         assert rms_rel(got, ref) < 1e-5
 
 
+def test_every_order_band_limited_by_a_low_linear_cut():
+    """A linear cut at 6.5 k_F (c1 = 6) on 64^3 keeps 4 c1 < N/2, so orders 2, 3
+    and 4 each move only their band columns (B = 14, 20, 26) with no cut on the
+    higher orders: all orders against the oracle, and exact zeros where a mode
+    has |s_y| or s_z >= B."""
+    N, L, n_max = 64, 500.0, 5
+    kF = 2 * math.pi / L
+    errs = _parity_case(N, L, n_max, 61, kcut_lin=kF * 6.5)
+    for (n, which), e in errs.items():
+        assert e < (1e-5 if n == 2 else 1e-4), (n, which, e)
+    plan = g.Plan(N, n_max, L, kcut_lin=kF * 6.5)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, 61, kcut_lin=kF * 6.5)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    sp = g.run_orders(plan, to_dev(ref1)[None])
+    sy = np.abs(np.fft.fftfreq(N, 1.0 / N).astype(int))[None, :, None]
+    kz = np.arange(N // 2)[None, None, :]
+    for m, B in ((2, 14), (3, 20), (4, 26)):
+        out = np.broadcast_to((sy >= B) | (kz >= B), (N, N, N // 2))
+        for w in range(2):
+            assert np.all(host(sp[0, m - 2, w])[out] == 0), (m, w)
+
+
 def test_resume_equals_full_run_bitwise():
     N, L, n_max = 64, 400.0, 5
     plan = g.Plan(N, n_max, L)
