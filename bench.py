@@ -334,6 +334,7 @@ def run_gpu(args, rank, world):
     del ws
     div = divergence_section(args, N, L, B, d1, spectra, stream) if rank == 0 else None
     mixed = mixed_batch(args) if rank == 0 and not args.quick else None
+    fftcmp = cufft_comparator(N, L) if rank == 0 else None
     emu = emulator_section(args) if rank == 0 and not args.quick else None
     if rank != 0:
         if dist:
@@ -383,6 +384,7 @@ def run_gpu(args, rank, world):
                             "value": round(B * N ** 3 * (N_MAX - 1) / graph_ms / 1e3, 1),
                             "unit": "Mcells*orders/s (orders 2..5, one graph launch, IC excluded)"},
         "mixed_batch": mixed,
+        "fft_vs_cufft": fftcmp,
         "emulator": emu,
         "divergence_form": div,
     }
@@ -488,12 +490,53 @@ def mixed_batch(args):
             "bitwise_equal_to_eager": bool(same)}
 
 
+def cufft_comparator(N, L):
+    """Timing comparator only, not on the library's path: the library's 3D
+    backward (C2R) and forward (R2C) transforms of four N^3 fields against
+    cuFFT's (through torch.fft, which calls cuFFT) on the same fields, after
+    warm-up (cuFFT's plans are cached by torch). Both unnormalised on the
+    backward side; cuFFT's half spectrum keeps the kz = N/2 plane, which the
+    library omits (zero by construction). Inputs of 2 GiB: larger than L2."""
+    import torch
+    from paper_1807_04215_gb300 import gridspt as g
+    plan = g.Plan(N, N_MAX, L)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    F = 4
+    spec = torch.randn(F, N, N, N // 2, dtype=torch.complex64, device="cuda", generator=gen)
+    real = torch.empty(F, N, N, N, dtype=torch.float32, device="cuda")
+    spec_cu = torch.zeros(F, N, N, N // 2 + 1, dtype=torch.complex64, device="cuda")
+    spec_cu[..., : N // 2] = spec
+    dims = (-3, -2, -1)
+
+    def per_field_ms(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return round(e0.elapsed_time(e1) / reps / F, 4)
+
+    out = {"fields": f"{F} x {N}^3 FP32", "comparator": "cuFFT through torch.fft (timing only)"}
+    out["library_c2r_ms_per_field"] = per_field_ms(lambda: g.c2r(plan, spec, out=real))
+    out["cufft_c2r_ms_per_field"] = per_field_ms(lambda: torch.fft.irfftn(spec_cu, s=(N, N, N), dim=dims,
+                                                                           norm="forward"))
+    out["library_r2c_ms_per_field"] = per_field_ms(lambda: g.r2c(plan, real, out=spec))
+    out["cufft_r2c_ms_per_field"] = per_field_ms(lambda: torch.fft.rfftn(real, dim=dims))
+    del spec, real, spec_cu
+    torch.cuda.empty_cache()
+    return out
+
+
 def emulator_section(args):
     """P-term emulator: 256-point Latin hypercube over (sigma_8, n_s, Gamma),
     GridSPT at 256^3, L = 1000 Mpc/h, n_max = 5, 4 seeds per point, P22, P13,
     P33, P24, P15 in 32 log bins over 0.01-0.3 h/Mpc; 3-128-128-160 SiLU network
     (bf16 weights and activations, FP32 accumulation) trained with the
-    library's kernels; judged by GridSPT on 32 held-out points."""
+    library's kernels; its error measured by GridSPT on 32 held-out points."""
     import numpy as np
     import torch
     from paper_1807_04215_gb300 import emulator as E
