@@ -334,7 +334,7 @@ def run_gpu(args, rank, world):
     del ws
     div = divergence_section(args, N, L, B, d1, spectra, stream) if rank == 0 else None
     mixed = mixed_batch(args) if rank == 0 and not args.quick else None
-    fftcmp = cufft_comparator(N, L) if rank == 0 else None
+    fftcmp = cufft_comparator(N, L, tuning) if rank == 0 else None
     emu = emulator_section(args) if rank == 0 and not args.quick else None
     if rank != 0:
         if dist:
@@ -490,16 +490,19 @@ def mixed_batch(args):
             "bitwise_equal_to_eager": bool(same)}
 
 
-def cufft_comparator(N, L):
+def cufft_comparator(N, L, tuning):
     """Timing comparator only, not on the library's path: the library's 3D
     backward (C2R) and forward (R2C) transforms of four N^3 fields against
     cuFFT's (through torch.fft, which calls cuFFT) on the same fields, after
     warm-up (cuFFT's plans are cached by torch). Both unnormalised on the
     backward side; cuFFT's half spectrum keeps the kz = N/2 plane, which the
-    library omits (zero by construction). Inputs of 2 GiB: larger than L2."""
+    library omits (zero by construction). Inputs of 2 GiB: larger than L2. The
+    library's transforms use the tile variants the autotuner chose for the
+    workload."""
     import torch
     from paper_1807_04215_gb300 import gridspt as g
     plan = g.Plan(N, N_MAX, L)
+    g.set_tuning(plan, tuning)
     gen = torch.Generator(device="cuda").manual_seed(0)
     F = 4
     spec = torch.randn(F, N, N, N // 2, dtype=torch.complex64, device="cuda", generator=gen)
@@ -520,7 +523,8 @@ def cufft_comparator(N, L):
         torch.cuda.synchronize()
         return round(e0.elapsed_time(e1) / reps / F, 4)
 
-    out = {"fields": f"{F} x {N}^3 FP32", "comparator": "cuFFT through torch.fft (timing only)"}
+    out = {"fields": f"{F} x {N}^3 FP32", "comparator": "cuFFT through torch.fft (timing only)",
+           "library_tuning": list(tuning)}
     out["library_c2r_ms_per_field"] = per_field_ms(lambda: g.c2r(plan, spec, out=real))
     out["cufft_c2r_ms_per_field"] = per_field_ms(lambda: torch.fft.irfftn(spec_cu, s=(N, N, N), dim=dims,
                                                                            norm="forward"))
