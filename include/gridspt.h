@@ -80,6 +80,14 @@ typedef struct {
                          <= 0 selects 2 k_Ny / (n_max + 1), k_Ny = pi N / L */
     double kcut_nl;   /* sharp-k cut applied to delta_n, theta_n for n >= 2;
                          <= 0 means none (only the Nyquist modes are zeroed) */
+    int32_t truncate; /* 1: every order j >= 2 formed by gridspt_run_orders is cut at
+                         min(j, n_max + 1 - j) K_c (|k| kept below it; K_c = the
+                         cut on delta_1), which is all that the orders above it
+                         need for their modes below K_c: delta_n, theta_n at
+                         |k| <= K_c equal those of the full recursion up to
+                         rounding, the modes above the cut are zero, and the
+                         passes of the cut orders move only their band columns.
+                         Nine-term form only. 0 (default): no such cut. */
 } gridspt_desc;
 
 /* Linear spectrum parameters: P(k) = A k^{n_s} T_BBKS(k / Gamma)^2, A fixed by

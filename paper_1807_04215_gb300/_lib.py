@@ -14,7 +14,7 @@ c_double = ctypes.c_double
 class GridsptDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_max", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("box", ctypes.c_double), ("kcut_lin", ctypes.c_double),
-                ("kcut_nl", ctypes.c_double)]
+                ("kcut_nl", ctypes.c_double), ("truncate", ctypes.c_int32)]
 
 
 class GridsptCosmo(ctypes.Structure):

@@ -27,6 +27,7 @@ struct gridspt_plan_s {
     float2* tw = nullptr;   // device: N entries, then the tables of the smaller sizes (sub_off)
     long long sub_off[kNumSizes] = {};   // offset in tw of the table of kSizes[i] < N, else -1
     long long s2_lin;       // keep 0 < |s|^2 <= s2_lin in delta_1
+    double r_lin = 0.0;     // the linear cut K_c / k_F
     long long s2_nl;        // < 0: no cut on higher orders
     int device = 0;
     long long pb_top = -1;  // cache of the last power-launch byte count (profiling only)
@@ -279,6 +280,9 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     if (d->form != GRIDSPT_FORM_NINE_TERM && d->form != GRIDSPT_FORM_DIVERGENCE)
         return fail(GRIDSPT_E_INVALID, "form=%d: must be GRIDSPT_FORM_NINE_TERM (0) or GRIDSPT_FORM_DIVERGENCE (1)",
                     d->form);
+    if (d->truncate != 0 && d->truncate != 1) return fail(GRIDSPT_E_INVALID, "truncate=%d: must be 0 or 1", d->truncate);
+    if (d->truncate && d->form != GRIDSPT_FORM_NINE_TERM)
+        return fail(GRIDSPT_E_INVALID, "truncate=1 needs the nine-term form");
     gridspt_plan_s* p = new (std::nothrow) gridspt_plan_s();
     if (!p) return fail(GRIDSPT_E_NOMEM, "host allocation failed");
     p->d = *d;
@@ -288,6 +292,7 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     p->geo.kF = 2.0 * M_PI / d->box;
     const double r = d->kcut_lin > 0 ? d->kcut_lin * d->box / (2.0 * M_PI) : (double)N / (d->n_max + 1);
     p->s2_lin = (long long)std::floor(r * r);
+    p->r_lin = r;
     if (d->kcut_nl > 0) {
         const double rn = d->kcut_nl * d->box / (2.0 * M_PI);
         p->s2_nl = (long long)std::floor(rn * rn);
@@ -576,6 +581,19 @@ void order1_band(const gridspt_plan_s* p, XExpArgs& xa, YZExpArgs& ya, YZExpArgs
     set_band(p, (int)std::floor(std::sqrt((double)p->s2_lin)) + 1, xa, ya, za, fx, fy_in, fy_out);
 }
 
+// Cut on an order m >= 2 formed in this call (< 0: none): the higher-order cut
+// s2_nl and, with truncate, |s| <= min(m, n_max + 1 - m) K_c / k_F, all that
+// the orders above m use of it for their modes below K_c.
+long long order_cut(const gridspt_plan_s* p, int m) {
+    long long c = p->s2_nl;
+    if (p->d.truncate) {
+        const double rt = std::min(m, p->d.n_max + 1 - m) * p->r_lin;
+        const long long t = (long long)std::floor(rt * rt);
+        c = c < 0 ? t : std::min(c, t);
+    }
+    return c;
+}
+
 // Band of an order m >= 2 formed in this call (0: none). Every component of
 // an order-1 mode is at most c1 = floor(sqrt(s2_lin)); a product of fields of
 // orders a + b = m then has components at most m c1, and while m c1 < N/2 no
@@ -588,8 +606,9 @@ void order1_band(const gridspt_plan_s* p, XExpArgs& xa, YZExpArgs& ya, YZExpArgs
 int order_band(const gridspt_plan_s* p, int m, int start) {
     const long long c1 = (long long)std::floor(std::sqrt((double)p->s2_lin));
     long long c = (start == 2 && 2 * m * c1 < p->geo.N) ? m * c1 : -1;
-    if (p->s2_nl >= 0) {
-        const long long cn = (long long)std::floor(std::sqrt((double)p->s2_nl));
+    const long long cut = order_cut(p, m);
+    if (cut >= 0) {
+        const long long cn = (long long)std::floor(std::sqrt((double)cut));
         c = c < 0 ? cn : std::min(c, cn);
     }
     return c < 0 ? 0 : (int)(c + 1);
@@ -625,7 +644,7 @@ gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* 
     xa.out = xs;
     xa.out_stride = F;
     xa.fwd_first = fwd ? 1 : 0;
-    xa.s2_nl = p->s2_nl;
+    xa.s2_nl = m >= 2 ? order_cut(p, m) : p->s2_nl;
     YZExpArgs ya{}, za{};
     ya.in = xs;
     ya.in_stride = F;
@@ -835,7 +854,8 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
                 CKP(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, dk, dk, F, 2, 1.0f, s), "z r2c");
                 CKP(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 1, 0, -1, s), "y pass fwd");
                 if (m == n_max) {
-                    CKP(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 1, p->s2_nl, s), "x pass fwd");
+                    CKP(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 1, order_cut(p, m), s),
+                        "x pass fwd");
                     break;
                 }
             }

@@ -40,16 +40,19 @@ class Plan:
 
     FORMS = {"nine_term": 0, "divergence": 1}
 
-    def __init__(self, n, n_max, box, batch=1, kcut_lin=0.0, kcut_nl=0.0, form="nine_term"):
+    def __init__(self, n, n_max, box, batch=1, kcut_lin=0.0, kcut_nl=0.0, form="nine_term", truncate=False):
         """form: "nine_term" (the paper's bilinear sources) or "divergence"
         (A_n = div sum delta_m u_{n-m}, B_n = lap sum u_m . u_{n-m} / 2; equal in
-        band, four real fields per order)."""
+        band, four real fields per order). truncate: cut every order j >= 2 at
+        min(j, n_max + 1 - j) K_c (outputs at |k| <= K_c unchanged; nine-term
+        form only)."""
         self.lib = _lib.load()
         if form not in self.FORMS:
             raise ValueError(f"form must be one of {sorted(self.FORMS)}")
         self.desc = Desc(n, n_max, box, batch, kcut_lin, kcut_nl)
         self.form = form
-        d = _lib.GridsptDesc(n, n_max, batch, self.FORMS[form], box, kcut_lin, kcut_nl)
+        self.truncate = bool(truncate)
+        d = _lib.GridsptDesc(n, n_max, batch, self.FORMS[form], box, kcut_lin, kcut_nl, int(bool(truncate)))
         h = ctypes.c_void_p()
         _lib.check("gridspt_plan_create", self.lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h

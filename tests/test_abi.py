@@ -41,7 +41,7 @@ def test_plan_create_rejects_bad_sizes_before_touching_cuda(lib):
     from paper_1807_04215_gb300 import _lib
     for n, n_max, box in [(10, 3, 100.0), (2048, 3, 100.0), (7, 3, 100.0), (64, 0, 100.0), (64, 9, 100.0),
                           (64, 3, -1.0)]:
-        d = _lib.GridsptDesc(n, n_max, 1, 0, box, 0.0, 0.0)
+        d = _lib.GridsptDesc(n, n_max, 1, 0, box, 0.0, 0.0, 0)
         h = ctypes.c_void_p()
         st = lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h))
         assert st == 1, (n, n_max, box)
@@ -52,11 +52,21 @@ def test_plan_create_rejects_bad_sizes_before_touching_cuda(lib):
 def test_plan_create_rejects_unknown_source_form(lib):
     from paper_1807_04215_gb300 import _lib
     for form in (-1, 2, 7):
-        d = _lib.GridsptDesc(64, 3, 1, form, 100.0, 0.0, 0.0)
+        d = _lib.GridsptDesc(64, 3, 1, form, 100.0, 0.0, 0.0, 0)
         h = ctypes.c_void_p()
         assert lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1, form
         assert h.value is None
         assert b"form" in lib.gridspt_last_error()
+
+
+def test_plan_create_rejects_bad_truncation(lib):
+    from paper_1807_04215_gb300 import _lib
+    for form, trunc in ((0, 2), (0, -1), (1, 1)):      # bad value; divergence form with truncation
+        d = _lib.GridsptDesc(64, 3, 1, form, 100.0, 0.0, 0.0, trunc)
+        h = ctypes.c_void_p()
+        assert lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1, (form, trunc)
+        assert h.value is None
+        assert b"truncate" in lib.gridspt_last_error()
 
 
 def test_null_plan_is_rejected(lib):

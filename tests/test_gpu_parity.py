@@ -316,6 +316,34 @@ def test_every_order_band_limited_by_a_low_linear_cut():
             assert np.all(host(sp[0, m - 2, w])[out] == 0), (m, w)
 
 
+@pytest.mark.parametrize("N,L,n_max,seed", [(64, 500.0, 5, 71), (48, 300.0, 4, 72)])
+def test_truncated_orders_match_the_oracle_below_the_cut(N, L, n_max, seed):
+    """truncate=1 cuts every order j >= 2 at min(j, n_max + 1 - j) K_c, all that
+    the orders above it use for their modes below K_c: delta_n, theta_n on the
+    modes |k| <= K_c against the full FP64 oracle recursion (the field bars of
+    the default path, over those modes), and exact zeros above each order's
+    cut."""
+    plan = g.Plan(N, n_max, L, truncate=True)
+    ref1 = spt.linear_field(N, L, n_max, COSMO, seed)
+    ref1 = inputs.half_to_full(inputs.full_to_half(ref1).astype(np.complex64))
+    sp = g.run_orders(plan, to_dev(ref1)[None])
+    dk, tk = spt.run_orders(ref1, L, n_max)
+    r = N / (n_max + 1)
+    s = np.fft.fftfreq(N, 1.0 / N).astype(np.int64)
+    s2 = s[:, None, None] ** 2 + s[None, :, None] ** 2 + np.arange(N // 2)[None, None, :] ** 2
+    w = np.full(s2.shape, 2.0)
+    w[:, :, 0] = 1.0
+    inb = s2 <= math.floor(r * r)
+    for n in range(2, n_max + 1):
+        cut = math.floor((min(n, n_max + 1 - n) * r) ** 2)
+        for which, ref in ((0, dk[n]), (1, tk[n])):
+            got = host(sp[0, n - 2, which])
+            half = ref[:, :, : N // 2]
+            err = math.sqrt(np.sum((w * np.abs(got - half) ** 2)[inb]) / np.sum((w * np.abs(half) ** 2)[inb]))
+            assert err < (1e-5 if n == 2 else 1e-4), (n, which, err)
+            assert np.all(got[s2 > cut] == 0), (n, which)
+
+
 def test_resume_equals_full_run_bitwise():
     N, L, n_max = 64, 400.0, 5
     plan = g.Plan(N, n_max, L)

@@ -85,3 +85,39 @@ def test_orders_formed_from_a_band_limited_field_vanish_outside_their_band():
             assert outside.sum() > 0
             for f in (dk[m], tk[m]):
                 assert np.abs(f[outside]).max() <= 1e-12 * np.abs(f).max(), (kcut, m)
+
+
+def test_truncating_each_order_keeps_every_order_below_the_linear_cut():
+    """The identity behind the library's truncate option: cutting every order j
+    >= 2 at min(j, n_max + 1 - j) K_c right after it is formed leaves delta_n,
+    theta_n at |k| <= K_c as the full recursion has them. A mode of delta_n below
+    K_c sums products of an order-j mode and an order-(n - j) mode within
+    (n - j) K_c of it, so the order-j factor lies below (n + 1 - j) K_c <=
+    (n_max + 1 - j) K_c, besides its own band j K_c. Checked with the oracle's
+    own steps (derived fields, sources, forward transform) and the cut
+    inserted, against its untruncated recursion, FP64 on 32^3."""
+    from oracle import cosmology, spt
+    N, L, n_max = 32, 250.0, 5
+    d1 = spt.linear_field(N, L, n_max, cosmology.DEFAULT_COSMO, 7)
+    dk, tk = spt.run_orders(d1, L, n_max)
+    nyq = spt.nyquist_mask(N)
+    sx, sy, sz = spt.wave_indices(N)
+    s2 = (sx * sx + sy * sy + sz * sz).astype(np.float64)
+    r = N / (n_max + 1)
+    delta, theta, fields = [None, d1.copy()], [None, d1.copy()], {}
+    for n in range(2, n_max + 1):
+        fields[n - 1] = spt.derived_fields(delta[n - 1], theta[n - 1], L)
+        A, B = spt.sources(fields, n)
+        cdA, cdB, ctA, ctB = spt.recursion_coefficients(n)
+        dn, tn = spt.forward(cdA * A + cdB * B), spt.forward(ctA * A + ctB * B)
+        cut = math.floor((min(n, n_max + 1 - n) * r) ** 2)
+        for f in (dn, tn):
+            f[nyq] = 0.0
+            f[s2 > cut] = 0.0
+        delta.append(dn)
+        theta.append(tn)
+    inb = s2 <= math.floor(r * r)
+    for n in range(2, n_max + 1):
+        for full, cut_run in ((dk[n], delta[n]), (tk[n], theta[n])):
+            scale = np.abs(full[inb]).max()
+            assert np.abs(full[inb] - cut_run[inb]).max() <= 1e-12 * scale, n
