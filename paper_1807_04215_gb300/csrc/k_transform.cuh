@@ -213,6 +213,15 @@ k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restric
 }
 
 // ------------------------------------------------------------ x expansion
+// Blocks per SM the x pass is compiled for: two 512-thread blocks (64
+// registers a thread, a small spill) for the narrow tile of power-of-two
+// N >= 512, where one block of the natural ~86 registers leaves 16 warps per
+// SM; one elsewhere (smaller N and radix-3 sizes would spill heavily).
+template <int N, int TZ, int MODE>
+__host__ __device__ constexpr int xexp_min_blocks() {
+    return (MODE != 2 && fft_elems(N) == 8 && N >= 512 && TZ * Cfg<N>::PC <= 512) ? 2 : 1;
+}
+
 // Inputs: delta(k) and theta(k) columns along kx. Each output f is
 // kx^a * src (src = delta, theta, phi = theta / k^2 or 1) or a shell mask times
 // src, transformed backward along x. With FWD the inputs first hold the
@@ -225,15 +234,6 @@ k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restric
 // fields V_x, V_y, V_z, S are transformed forward along x and combined into
 // A = i k . V, B = -(k^2 / 2) S, delta = cdA A + cdB B, theta = ctA A + ctB B
 // (written to src0, src1 and finalised like MODE 1).
-// Blocks per SM the x pass is compiled for: two 512-thread blocks (64
-// registers a thread, a small spill) for the narrow tile of power-of-two
-// N >= 512, where one block of the natural ~86 registers leaves 16 warps per
-// SM; one elsewhere (smaller N and radix-3 sizes would spill heavily).
-template <int N, int TZ, int MODE>
-__host__ __device__ constexpr int xexp_min_blocks() {
-    return (MODE != 2 && fft_elems(N) == 8 && N >= 512 && TZ * Cfg<N>::PC <= 512) ? 2 : 1;
-}
-
 template <int N, int TZ, int MODE>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PC, xexp_min_blocks<N, TZ, MODE>())
 k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
