@@ -600,9 +600,10 @@ long long order_cut(const gridspt_plan_s* p, int m) {
 // product of the recursion up to order m wraps around the grid, so
 // delta_m(k), theta_m(k) vanish at every mode with a component |s_a| > m c1.
 // That holds when every lower order was formed here too (start == 2); stored
-// lower orders are not assumed band limited. With the cut on higher orders
-// (s2_nl >= 0) the finalising pass zeroes every |s|^2 > s2_nl, which bounds
-// the components by floor(sqrt(s2_nl)) whatever the products did.
+// lower orders are not assumed band limited. With a cut on order m
+// (order_cut >= 0: the higher-order cut, or truncate) the finalising pass
+// zeroes every |s|^2 above it, which bounds the components by the cut's
+// floor(sqrt) whatever the products did.
 int order_band(const gridspt_plan_s* p, int m, int start) {
     const long long c1 = (long long)std::floor(std::sqrt((double)p->s2_lin));
     long long c = (start == 2 && 2 * m * c1 < p->geo.N) ? m * c1 : -1;
