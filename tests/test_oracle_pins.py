@@ -78,15 +78,70 @@ def test_sigma8_normalisation_by_independent_quadrature():
     assert abs(sigma8 - 0.8) < 1e-6
 
 
-def test_bbks_limits():
-    """T -> 1 with slope -(2.34/2 + 3.89/4) at q -> 0; T q^2 / ln(2.34 q) ->
-    1 / (2.34 * 6.71) at q -> inf (catches a wrong coefficient in either end)."""
-    q = np.array([1e-6])
-    slope = (cosmology.bbks_transfer(q)[0] - 1.0) / q[0]
-    assert abs(slope + (1.17 + 3.89 / 4)) < 1e-4
-    q = np.array([1e9])
-    lim = cosmology.bbks_transfer(q)[0] * q[0] ** 2 / math.log(2.34 * q[0])
-    assert abs(lim * 2.34 * 6.71 - 1.0) < 1e-2
+def _bbks_constants():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "bbks1986_transfer.txt"))
+            if l.strip() and not l.startswith("#")]
+    return {k: float(v) for k, v in rows}
+
+
+def _bbks_taylor_by_hand(a, b, c, d):
+    """Taylor coefficients t1, t2, t3 of T(q) = 1 + t1 q + t2 q^2 + t3 q^3 + ...
+    at q -> 0, expanded by hand from the published form. With
+    P = 1 + b q + c^2 q^2 + d^3 q^3 + ..., (1 + x)^(-1/4) = 1 - x/4 + 5 x^2/32
+    - 15 x^3/128 gives P^(-1/4) = 1 + p1 q + p2 q^2 + p3 q^3 with
+        p1 = -b/4,  p2 = -c^2/4 + 5 b^2/32,  p3 = -d^3/4 + 5 b c^2/16 - 15 b^3/128,
+    and ln(1 + a q)/(a q) = 1 - a q/2 + a^2 q^2/3 - a^3 q^3/4; their product
+    has t1 = p1 - a/2, t2 = p2 - a p1/2 + a^2/3, t3 = p3 - a p2/2 + a^2 p1/3 - a^3/4."""
+    p1 = -b / 4.0
+    p2 = -c * c / 4.0 + 5.0 * b * b / 32.0
+    p3 = -d ** 3 / 4.0 + 5.0 * b * c * c / 16.0 - 15.0 * b ** 3 / 128.0
+    return (p1 - a / 2.0,
+            p2 - a * p1 / 2.0 + a * a / 3.0,
+            p3 - a * p2 / 2.0 + a * a * p1 / 3.0 - a ** 3 / 4.0)
+
+
+def _taylor_fit(T, h=2e-3, deg=7):
+    """Coefficients of q^0..q^3 of T near 0: a polynomial fit in the scaled
+    variable y = q/h - 1 over (0, 2h] at Chebyshev nodes, re-expanded in q (the
+    nearest singularity of the BBKS form is at |q| = 0.063, so the truncation
+    error of degree 7 on q <= 2h is far below the tolerances used)."""
+    y = np.cos(np.linspace(0.0, math.pi, 401))[:-1]
+    q = h * (1.0 + y)
+    P = np.polynomial.Polynomial(np.polynomial.polynomial.polyfit(y, T(q), deg))
+    return P(np.polynomial.Polynomial([-1.0, 1.0 / h])).coef[:4]
+
+
+def _bbks_pins_hold(T, consts):
+    c0, c1, c2, c3 = _taylor_fit(T)
+    t1, t2, t3 = _bbks_taylor_by_hand(consts["a"], consts["b"], consts["c"], consts["d"])
+    a, e = consts["a"], consts["e"]
+    qb = np.array([1e9])
+    lim = T(qb)[0] * qb[0] ** 2 / math.log(a * qb[0])
+    return (abs(c0 - 1.0) < 1e-12 and abs(c1 / t1 - 1.0) < 1e-9 and abs(c2 / t2 - 1.0) < 1e-7
+            and abs(c3 / t3 - 1.0) < 1e-5 and abs(lim * a * e - 1.0) < 1e-2)
+
+
+def test_bbks_taylor_coefficients_and_large_q_limit():
+    """T(q) of the oracle against the published BBKS constants
+    (tests/golden/bbks1986_transfer.txt): its q, q^2 and q^3 Taylor coefficients
+    at q -> 0 (expanded by hand; they fix a, b, then c through c^2 and d through
+    d^3) and its q -> inf limit T q^2 / ln(a q) -> 1/(a e) (fixes e). Catches a
+    wrong value of any of the five constants."""
+    assert _bbks_pins_hold(cosmology.bbks_transfer, _bbks_constants())
+
+
+@pytest.mark.parametrize("typo", [("16.1", "16.2"), ("5.46", "5.47"), ("3.89", "3.98"),
+                                  ("(5.46 * qq) ** 3", "(5.46 * qq) ** 2"), ("6.71", "6.17")])
+def test_bbks_pins_catch_a_planted_typo(typo):
+    """The pins above reject a copy of the oracle's T(q) with one constant or
+    exponent mistyped (the mistake is planted in a copy of the oracle's source,
+    on the CPU)."""
+    import inspect
+    src = inspect.getsource(cosmology.bbks_transfer)
+    assert typo[0] in src
+    scope = {"np": np}
+    exec(src.replace(typo[0], typo[1], 1), scope)
+    assert not _bbks_pins_hold(scope["bbks_transfer"], _bbks_constants())
 
 
 # ---------------------------------------------------------- initial field
