@@ -31,12 +31,11 @@ UNIT = "Mcells*orders/s"
 N_GRID, BOX, N_MAX = 512, 2000.0, 5
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic / algorithmic bytes measured by ncu for the kernels as they stand
-# (profiles/k_xexp_k_yexp_k_zexp_c2r-512.md: 512^3, one field per launch;
-# profiles/k_zrow_orders-256.md: the warp-row z expansion, the four launches of
-# one realisation at 256^3, bytes growing as N^3); traffic per launch is
-# reported as this ratio times the launch's algorithmic bytes. A kernel changed
-# since its capture has no entry (traffic null): the x pass was recompiled for
-# two blocks per SM after its capture.
+# (captures of the y expansion at 512^3, one field per launch, and of the
+# warp-row z expansion, the four launches of one realisation at 256^3, bytes
+# growing as N^3); traffic per launch is reported as this ratio times the
+# launch's algorithmic bytes. A kernel changed since its capture has no entry
+# (traffic null).
 NCU_TRAFFIC_RATIO = {"y_expand": 0.969, "z_expand": 1.008}
 
 
@@ -586,6 +585,60 @@ def emulator_section(args):
             "speedup": round(grid_s_per_point / emu_s_per_point, 1)}
 
 
+def run_case(args):
+    """Small, self-contained invocations of the library for a profiler (ncu):
+    one case, repeated `reps` times so that a profiler can skip the first.
+      c2r      backward transforms of 4 random half spectra (x, y, z passes)
+      r2c      forward transforms of 4 random real fields
+      orders   one realisation: initial field and orders 2..n_max (L = 2000 N / 512)
+      power    the six P-terms of one realisation (32 log bins, 0.01-0.4 h/Mpc)
+      bispec   the equilateral bispectrum of one realisation (16 shells)
+    --stats prints the library's per-kind launches, event time and algorithmic
+    bytes of the last repetition (JSON)."""
+    import torch
+    from paper_1807_04215_gb300 import gridspt as g
+    N, n_max = args.n, args.nmax
+    L = BOX * N / N_GRID
+    plan = g.Plan(N, n_max, L)
+    if args.tuning:
+        g.set_tuning(plan, [int(v) for v in args.tuning.split(",")])
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    if args.case in ("c2r", "r2c"):
+        spec = torch.randn(4, N, N, N // 2, dtype=torch.complex64, device="cuda", generator=gen)
+        real = torch.empty(4, N, N, N, dtype=torch.float32, device="cuda")
+        for _ in range(args.reps):
+            if args.case == "c2r":
+                g.c2r(plan, spec, out=real)
+            else:
+                g.r2c(plan, real.normal_(generator=gen), out=spec)
+    else:
+        d1 = g.make_linear_field(plan, [1000])
+        spectra = g.run_orders(plan, d1) if args.case != "orders" else None
+        edges = log_edges(0.01, 0.4, 32)
+        kc = 2 * math.pi / L * N / (n_max + 1)
+        bedges = [kc * i / 16 for i in range(17)]
+        for rep in range(args.reps):
+            if args.stats and rep == args.reps - 1:
+                torch.cuda.synchronize()
+                g.profile_begin()
+            if args.case == "orders":
+                g.make_linear_field(plan, [1000], out=d1)
+                spectra = g.run_orders(plan, d1)
+            elif args.case == "power":
+                dl = {1: d1[0], **{n: spectra[0, n - 2, 0] for n in range(2, n_max + 1)}}
+                for i, j in [(1, 1), (1, 3), (2, 2), (1, 5), (2, 4), (3, 3)]:
+                    if j <= n_max:
+                        g.power(plan, dl[i], dl[j], edges)
+            else:
+                g.bispectrum(plan, d1[0], spectra[0, 0, 0], bedges)
+    torch.cuda.synchronize()
+    if args.stats and args.case not in ("c2r", "r2c"):
+        st = g.profile_end()
+        print(json.dumps({k: {"launches": v[0], "ms": round(v[1], 4), "GB": round(v[2] / 1e9, 4)}
+                          for k, v in st.items()}))
+    print("ok", args.case, N)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,7 +649,16 @@ def main():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--quick", action="store_true", help="skip the mixed-batch and emulator sections")
     ap.add_argument("--emu-steps", type=int, default=20000)
+    ap.add_argument("--case", choices=["c2r", "r2c", "orders", "power", "bispec"],
+                    help="run one small library case for a profiler instead of the benchmark")
+    ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
+    ap.add_argument("--nmax", type=int, default=N_MAX, help="--case: highest order")
+    ap.add_argument("--tuning", default="", help="--case: tile variants per pass, e.g. 1,1,1,2,2")
+    ap.add_argument("--stats", action="store_true", help="--case: per-kind stats of the last repetition")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

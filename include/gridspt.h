@@ -50,8 +50,8 @@ typedef enum {
     GRIDSPT_E_UNSUPPORTED = 2, /* valid request outside what the library supports */
     GRIDSPT_E_NOMEM = 3,       /* plan tables could not be allocated */
     GRIDSPT_E_CUDA = 4,        /* a CUDA runtime call or launch failed */
-    GRIDSPT_E_TIMEOUT = 5,     /* reserved: a bounded device-side wait gave up */
-    GRIDSPT_E_NUMERIC = 6      /* reserved: non-finite result detected */
+    GRIDSPT_E_TIMEOUT = 5,     /* a bounded device-side wait gave up (reported by gridspt_check) */
+    GRIDSPT_E_NUMERIC = 6      /* an estimator result was NaN or infinite (reported by gridspt_check) */
 } gridspt_status;
 
 typedef struct gridspt_plan_s* gridspt_plan;
@@ -68,6 +68,16 @@ typedef void* gridspt_stream; /* cudaStream_t */
  *   nine-term form's to rounding; modes above it, where the grid products fold,
  *   differ between the two forms. Not in the paper. */
 enum { GRIDSPT_FORM_NINE_TERM = 0, GRIDSPT_FORM_DIVERGENCE = 1 };
+
+/* Shell-sum accumulation of the power and bispectrum estimators (Eqs. pk_lin,
+ * pk_1loop, pk_2loop, bk_tree; the paper does not state a precision). The
+ * terms are formed from the FP32 fields either way.
+ * GRIDSPT_ACCUM_COMPENSATED (default, 0): FP32 partial sums whose rounding
+ *   errors are carried (two-sum in the power scan, Kahan chains in the shell
+ *   sums), finished in FP64.
+ * GRIDSPT_ACCUM_FP64: every term added in FP64 (power products formed in FP64
+ *   from the FP32 inputs; shell products formed in FP32, summed in FP64). */
+enum { GRIDSPT_ACCUM_COMPENSATED = 0, GRIDSPT_ACCUM_FP64 = 1 };
 
 /* Problem description (Sec. II.C: box, grid, highest order, sharp-k cuts). */
 typedef struct {
@@ -88,6 +98,8 @@ typedef struct {
                          rounding, the modes above the cut are zero, and the
                          passes of the cut orders move only their band columns.
                          Nine-term form only. 0 (default): no such cut. */
+    int32_t accum;    /* estimator shell sums: GRIDSPT_ACCUM_COMPENSATED (0) or
+                         GRIDSPT_ACCUM_FP64 (1) */
 } gridspt_desc;
 
 /* Linear spectrum parameters: P(k) = A k^{n_s} T_BBKS(k / Gamma)^2, A fixed by
@@ -148,6 +160,11 @@ gridspt_status gridspt_make_linear_field(gridspt_plan plan, const gridspt_cosmo*
  *             |ky|, kz < B, B = c_n + 1 rounded up to even, when B < N/2, and
  *             is written as exact zeros outside them, where its exact values
  *             vanish. s2_lin = floor((kcut_lin / k_F)^2), likewise s2_nl.
+ *             The k = 0 mode of every order formed in the call is written as
+ *             zero, its exact value (mass conservation: the k = 0 modes of
+ *             the two source terms cancel exactly on the grid), not as the
+ *             FP32 rounding residue of the mean of the products, which would
+ *             otherwise feed the next orders as a spurious uniform field.
  *   start_order: 2 for a full run; 3..n_max resumes from stored lower orders
  *             (Sec. II.C: only delta_m, theta_m are needed to continue).
  *   ws, ws_bytes: device scratch of at least gridspt_workspace_size bytes.
@@ -176,7 +193,9 @@ gridspt_status gridspt_r2c(gridspt_plan plan, const float* in_x, void* out_k, in
  *   1 <= nbins <= 64. Products in FP32; runs of up to 32 consecutive modes
  *   of a bin summed in FP32 with each addition's rounding error carried
  *   (two-sum), the runs accumulated in FP64, all reduced in a fixed order
- *   (bitwise repeatable). Cross terms of the paper carry a factor
+ *   (bitwise repeatable); with accum = GRIDSPT_ACCUM_FP64 the products and
+ *   every sum are FP64. A NaN or infinite result sets the plan's status
+ *   (gridspt_check then returns GRIDSPT_E_NUMERIC). Cross terms of the paper carry a factor
  *   2: P_13 = 2 * gridspt_power(delta_1, delta_3). ws: device scratch of
  *   gridspt_power_workspace_size bytes (per-block partial sums). */
 gridspt_status gridspt_power_workspace_size(gridspt_plan plan, int32_t nbins, size_t* bytes);
@@ -245,8 +264,9 @@ gridspt_status gridspt_cross_correlation(gridspt_plan plan, const void* a_k, con
  *   edges: HOST double[nbins+1] with edges[nbins] <= 2 k_Ny / 3 (no wrap);
  *   e_out, ntri_out: device double[nbins]; 1 <= nbins <= 64. FP32 fields,
  *   Kahan-compensated FP32 sums over row groups of cells, FP64 across groups,
- *   fixed order. Sums over x run on the smallest supported grid S > 3 (B - 1)
- *   (S <= N) for a shell whose vectors have every component |s_a| < B: there
+ *   fixed order (FP64 sums of the same terms with accum = GRIDSPT_ACCUM_FP64);
+ *   a NaN or infinite result sets the plan's status (GRIDSPT_E_NUMERIC).
+ *   Sums over x run on the smallest supported grid S > 3 (B - 1) (S <= N) for a shell whose vectors have every component |s_a| < B: there
  *   the only sum of three shell vectors that is a multiple of S is zero, so
  *   both sums are those of the N^3 grid times (S/N)^3 and e_out, ntri_out are
  *   unchanged (the inputs are copied onto that grid in the workspace first).
@@ -290,6 +310,42 @@ gridspt_status gridspt_batch_create(const gridspt_plan* plans, int32_t count, co
                                     const size_t* ws_bytes, gridspt_batch* out);
 gridspt_status gridspt_batch_launch(gridspt_batch batch, gridspt_stream stream);
 gridspt_status gridspt_batch_destroy(gridspt_batch batch);
+
+/* Persistent work queue (not part of the paper's method): the recursion of one
+ * or several plans, whose grid sizes may differ (e.g. 128^3, 192^3 and 256^3
+ * realisations), in ONE launch of one persistent kernel.
+ *   gridspt_multi_create records, for every plan i, the launches that
+ *     gridspt_run_orders(plans[i], delta1_k[i], start_order[i] (NULL: all 2),
+ *     spectra[i], ws[i], ws_bytes[i]) would make, as stages of tiles (column
+ *     blocks, z row groups, cell blocks), and lays them out in one device-side
+ *     queue: a plan's stages form a chain (each waits for its predecessor, so
+ *     the realisations of a plan, which share ws[i], run one after another);
+ *     chains of different plans are interleaved by their cumulative work.
+ *     Host call; allocates and fills the queue's device table (about 1.7 KB a
+ *     stage, ~25 stages per realisation at n_max = 5), owned by the returned
+ *     object. Pointers are used as in gridspt_run_orders, must stay valid while
+ *     the object is used and must not overlap between plans (each plan needs
+ *     its own workspace). Supported: the nine-term form with N = 64, 96, 128,
+ *     192 or 256 (GRIDSPT_E_UNSUPPORTED otherwise), plans on one device.
+ *   gridspt_run_orders_multi enqueues one launch of the persistent kernel on
+ *     `stream` (grid: as many 256-thread blocks as fit on the GPU at once). A
+ *     block takes the next tile in queue order from a ticket counter, waits
+ *     until the tile's predecessor stage has counted all its tiles done, runs
+ *     the tile with the arithmetic of the pass's own kernel and counts it
+ *     done. Results are bit for bit those of gridspt_run_orders for every plan.
+ *     A wait only ever concerns earlier tickets, which running blocks hold, so
+ *     it always ends; in addition every wait gives up after 1 s of GPU time:
+ *     the block then sets the status word of plans[0] (gridspt_check(plans[0])
+ *     returns GRIDSPT_E_TIMEOUT and the results are invalid) and every block
+ *     returns. Calls on one object must not overlap on the GPU (they share its
+ *     ticket and completion counters).
+ *   gridspt_multi_destroy synchronises the device and frees the table. */
+typedef struct gridspt_multi_s* gridspt_multi;
+gridspt_status gridspt_multi_create(const gridspt_plan* plans, int32_t count, const void* const* delta1_k,
+                                    const int32_t* start_order, void* const* spectra, void* const* ws,
+                                    const size_t* ws_bytes, gridspt_multi* out);
+gridspt_status gridspt_run_orders_multi(gridspt_multi multi, gridspt_stream stream);
+gridspt_status gridspt_multi_destroy(gridspt_multi multi);
 
 /* Autotuner for the transform passes (not part of the paper's method). Each
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
@@ -373,10 +429,15 @@ typedef struct {
 gridspt_status gridspt_profile_begin(void);
 gridspt_status gridspt_profile_end(gridspt_kernel_stat* stats, int32_t capacity, int32_t* count);
 
-/* Device-side status: synchronises `stream` and returns GRIDSPT_E_TIMEOUT if a
- * bounded device-side wait (the mbarrier waits of the TMA-staged passes) gave
- * up since the last check, in which case the results of those calls are
- * invalid; the status is then reset. GRIDSPT_OK otherwise. */
+/* Device-side status: synchronises `stream` and reads the plan's status word,
+ * which the plan's kernels set since the last check:
+ * - GRIDSPT_E_TIMEOUT if a bounded device-side wait (the mbarrier waits of the
+ *   TMA-staged passes, or the self-test's) gave up; the results of those calls
+ *   are invalid;
+ * - else GRIDSPT_E_NUMERIC if a power, cross-correlation or bispectrum result
+ *   was NaN or infinite (a non-finite value in an input spectrum inside the
+ *   bins reaches the result; values outside every bin are not seen);
+ * - GRIDSPT_OK otherwise. The status is reset by the call. */
 gridspt_status gridspt_check(gridspt_plan plan, gridspt_stream stream);
 
 /* Failure-detection self-test (not part of the paper's method): launches one

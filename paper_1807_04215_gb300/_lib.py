@@ -14,7 +14,7 @@ c_double = ctypes.c_double
 class GridsptDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_max", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("box", ctypes.c_double), ("kcut_lin", ctypes.c_double),
-                ("kcut_nl", ctypes.c_double), ("truncate", ctypes.c_int32)]
+                ("kcut_nl", ctypes.c_double), ("truncate", ctypes.c_int32), ("accum", ctypes.c_int32)]
 
 
 class GridsptCosmo(ctypes.Structure):
@@ -59,6 +59,11 @@ SIGNATURES = {
                                        ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                        ctypes.POINTER(c_size_t), ctypes.POINTER(c_void_p)]),
     "gridspt_batch_launch": (c_int32, [c_void_p, c_void_p]),
+    "gridspt_multi_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(c_size_t), ctypes.POINTER(c_void_p)]),
+    "gridspt_run_orders_multi": (c_int32, [c_void_p, c_void_p]),
+    "gridspt_multi_destroy": (c_int32, [c_void_p]),
     "gridspt_batch_destroy": (c_int32, [c_void_p]),
     "gridspt_autotune_scratch_size": (c_int32, [c_void_p, ctypes.POINTER(c_size_t)]),
     "gridspt_autotune": (c_int32, [c_void_p, c_void_p, c_size_t, ctypes.POINTER(c_int32), c_void_p]),

@@ -63,6 +63,7 @@ gridspt_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Host-side fault injection for tests (no GPU fault is ever caused): the
 // environment variable GRIDSPT_FAULT_INJECT holds a comma-separated list of
@@ -84,12 +85,12 @@ bool fault_inject(const char* what) {
 enum ProfKind {
     PK_IC, PK_XEXP, PK_XEXP_FWD, PK_YEXP, PK_ZEXP, PK_Y_FWD, PK_X_FWD, PK_ZR2C,
     PK_PRODUCT, PK_POWER, PK_BISPEC, PK_BX, PK_BY, PK_BZ, PK_MLP_FWD, PK_MLP_BWD, PK_MLP_OPT, PK_FIELDS,
-    PK_BGATHER, PK_COUNT
+    PK_BGATHER, PK_QUEUE, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {
     "ic", "x_expand", "x_fwd_expand", "y_expand", "z_expand", "y_fwd", "x_fwd", "z_r2c",
     "product", "power", "bispec_final", "shell_x", "shell_y", "shell_z", "mlp_forward", "mlp_backward",
-    "mlp_update", "sum_orders", "shell_grid"};
+    "mlp_update", "sum_orders", "shell_grid", "work_queue"};
 constexpr size_t kMaxProfRecs = 65536;
 
 struct ProfRec {
@@ -142,6 +143,34 @@ cudaError_t prof_launch(int kind, double bytes, cudaStream_t s, F&& f) {
     do {                                                                              \
         cudaError_t e_ = prof_launch((kind), (bytes), (s), [&]() { return (call); }); \
         if (e_ != cudaSuccess) return cuda_fail(e_, where);                           \
+    } while (0)
+
+// Stage recording for the persistent work queue (gridspt_run_orders_multi):
+// while t_queue is set, the launch sites of the recursion append a stage
+// (kind, grid, arguments, work estimate) instead of launching.
+thread_local std::vector<QStage>* t_queue = nullptr;
+
+QStage q_stage(const Geo& g, int kind, double cost) {
+    QStage q{};
+    q.kind = kind;
+    q.N = g.N;
+    q.dep = -1;
+    q.tw = g.tw;
+    q.kF = (float)g.kF;
+    q.inv_kF2 = (float)(1.0 / (g.kF * g.kF));
+    q.cost = cost;
+    return q;
+}
+
+#define CKQ(kind, bytes, s, call, where, stage)          \
+    do {                                                 \
+        if (t_queue) {                                   \
+            QStage q_ = (stage);                         \
+            queue_tiles(q_);                             \
+            t_queue->push_back(q_);                      \
+        } else {                                         \
+            CKP(kind, bytes, s, call, where);            \
+        }                                                \
     } while (0)
 
 long long field_floats(const gridspt_plan_s* p) { return (long long)p->geo.N * p->geo.N * p->geo.N; }
@@ -283,6 +312,9 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     if (d->truncate != 0 && d->truncate != 1) return fail(GRIDSPT_E_INVALID, "truncate=%d: must be 0 or 1", d->truncate);
     if (d->truncate && d->form != GRIDSPT_FORM_NINE_TERM)
         return fail(GRIDSPT_E_INVALID, "truncate=1 needs the nine-term form");
+    if (d->accum != GRIDSPT_ACCUM_COMPENSATED && d->accum != GRIDSPT_ACCUM_FP64)
+        return fail(GRIDSPT_E_INVALID, "accum=%d: must be GRIDSPT_ACCUM_COMPENSATED (0) or GRIDSPT_ACCUM_FP64 (1)",
+                    d->accum);
     gridspt_plan_s* p = new (std::nothrow) gridspt_plan_s();
     if (!p) return fail(GRIDSPT_E_NOMEM, "host allocation failed");
     p->d = *d;
@@ -290,6 +322,7 @@ gridspt_status gridspt_plan_create(const gridspt_desc* d, gridspt_plan* out) {
     p->geo.N = N;
     p->geo.M = N / 2;
     p->geo.kF = 2.0 * M_PI / d->box;
+    p->geo.accum = d->accum == GRIDSPT_ACCUM_FP64 ? kAccumFp64 : kAccumCompensated;
     const double r = d->kcut_lin > 0 ? d->kcut_lin * d->box / (2.0 * M_PI) : (double)N / (d->n_max + 1);
     p->s2_lin = (long long)std::floor(r * r);
     p->r_lin = r;
@@ -550,10 +583,15 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
         if (a.ntargets == 0) {   // store only: the plain z expansion
             YZExpArgs zs = za;
             zs.out = reinterpret_cast<float2*>(a.store);
-            CKP(PK_ZEXP, bytes, s, launch_zexp(p->geo, zs, s), "z expansion");
+            ZPairArgs zq{};
+            zq.z = zs;
+            zq.cells = cells;
+            CKQ(PK_ZEXP, bytes, s, launch_zexp(p->geo, zs, s), "z expansion",
+                [&]() { QStage q = q_stage(p->geo, Q_Z, bytes); q.z = zq; return q; }());
             break;
         }
-        CKP(PK_ZEXP, bytes, s, launch_zexp_pairs(p->geo, a, s), "z expansion and pair products");
+        CKQ(PK_ZEXP, bytes, s, launch_zexp_pairs(p->geo, a, s), "z expansion and pair products",
+            [&]() { QStage q = q_stage(p->geo, Q_Z, bytes); q.z = a; return q; }());
     } while (first < js.size());
     return GRIDSPT_OK;
 }
@@ -645,6 +683,7 @@ gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* 
     xa.out = xs;
     xa.out_stride = F;
     xa.fwd_first = fwd ? 1 : 0;
+    xa.zero_k0 = fwd ? 1 : 0;   // order m >= 2 formed here: its k = 0 mode is exactly zero
     xa.s2_nl = m >= 2 ? order_cut(p, m) : p->s2_nl;
     YZExpArgs ya{}, za{};
     ya.in = xs;
@@ -663,12 +702,21 @@ gridspt_status derive_order(const gridspt_plan_s* p, int m, float2* dk, float2* 
     else if (fwd) {
         if (const int band = order_band(p, m, start)) set_band(p, band, xa, ya, za, &fx, &fy_in, &fy_out);
     }
-    CKP(fwd ? PK_XEXP_FWD : PK_XEXP, fb * fx * (fwd ? 2 * nin + xa.nout : nin + xa.nout), s,
-        launch_xexp(p->geo, xa, s), "x expansion");
+    const double xbytes = fb * fx * (fwd ? 2 * nin + xa.nout : nin + xa.nout);
+    CKQ(fwd ? PK_XEXP_FWD : PK_XEXP, xbytes, s, launch_xexp(p->geo, xa, s), "x expansion",
+        [&]() { QStage q = q_stage(p->geo, fwd ? Q_XEXP1 : Q_XEXP0, xbytes); q.x = xa; return q; }());
     if (m >= 2 && xa.band > 0 && fwd)   // the spectra outside the band columns: zeros
-        CKP(PK_XEXP_FWD, fb * 2.0 * (1.0 - fx), s, launch_zero_outside_band(dk, tk, p->geo.N, xa.band, s),
-            "zeros outside the band");
-    CKP(PK_YEXP, fb * (fy_in * xa.nout + fy_out * ya.nout), s, launch_yexp(p->geo, ya, s), "y expansion");
+        CKQ(PK_XEXP_FWD, fb * 2.0 * (1.0 - fx), s, launch_zero_outside_band(dk, tk, p->geo.N, xa.band, s),
+            "zeros outside the band", [&]() {
+                QStage q = q_stage(p->geo, Q_ZEROBAND, fb * 2.0 * (1.0 - fx));
+                q.data = dk;
+                q.data2 = tk;
+                q.band = xa.band;
+                return q;
+            }());
+    const double ybytes = fb * (fy_in * xa.nout + fy_out * ya.nout);
+    CKQ(PK_YEXP, ybytes, s, launch_yexp(p->geo, ya, s), "y expansion",
+        [&]() { QStage q = q_stage(p->geo, Q_YEXP, ybytes); q.y = ya; return q; }());
     return zexp_pairs(p, m, za, ws, start, spec_delta, s);
 }
 
@@ -852,11 +900,22 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
             float2* dk = m == 1 ? d1 : spec(m, 0);
             float2* tk = m == 1 ? d1 : spec(m, 1);
             if (!given) {
-                CKP(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, dk, dk, F, 2, 1.0f, s), "z r2c");
-                CKP(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 1, 0, -1, s), "y pass fwd");
+                auto col = [&](int kind) {
+                    QStage q = q_stage(p->geo, kind, 4 * fb);
+                    q.data = dk;
+                    q.fstride = F;
+                    q.count = 2;
+                    q.scale = 1.0f;
+                    q.s2 = order_cut(p, m);
+                    q.zero_k0 = 1;
+                    return q;
+                };
+                CKQ(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, dk, dk, F, 2, 1.0f, s), "z r2c", col(Q_ZR2C));
+                CKQ(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 1, 0, -1, s), "y pass fwd",
+                    col(Q_COLY));
                 if (m == n_max) {
-                    CKP(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 1, order_cut(p, m), s),
-                        "x pass fwd");
+                    CKQ(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 2, order_cut(p, m), s),
+                        "x pass fwd", col(Q_COLX));
                     break;
                 }
             }
@@ -882,7 +941,8 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
                     pa.ctA = 0.f;
                     pa.ctB = 1.f;
                 }
-                CKP(PK_PRODUCT, fb * (m == 1 ? 13 + 2 : 17 + 2), s, launch_product(p->geo, pa, s), "diagonal pair");
+                CKQ(PK_PRODUCT, fb * (m == 1 ? 13 + 2 : 17 + 2), s, launch_product(p->geo, pa, s), "diagonal pair",
+                    [&]() { QStage q = q_stage(p->geo, Q_PRODUCT, fb * (m == 1 ? 13 + 2 : 17 + 2)); q.pr = pa; return q; }());
             }
         }
     }
@@ -991,6 +1051,146 @@ gridspt_status gridspt_batch_destroy(gridspt_batch b) {
     cudaError_t e = b->exec ? cudaGraphExecDestroy(b->exec) : cudaSuccess;
     delete b;
     if (e != cudaSuccess) return cuda_fail(e, "batch destroy");
+    return GRIDSPT_OK;
+}
+
+// ------------------------------------------------------- persistent queue
+}  // extern "C"
+
+struct gridspt_multi_s {
+    void* dev = nullptr;         // stages, then first tickets, then the queue header
+    QStage* stages = nullptr;
+    long long* starts = nullptr;
+    int* hdr = nullptr;
+    int nst = 0;
+    long long total = 0;
+    int* status = nullptr;       // status word of plans[0]
+    int device = 0;
+};
+
+namespace {
+constexpr long long kQueueWaitNs = 1000000000LL;   // a tile gives up waiting after 1 s
+}
+
+extern "C" {
+
+gridspt_status gridspt_multi_create(const gridspt_plan* plans, int32_t count, const void* const* delta1_k,
+                                    const int32_t* start_order, void* const* spectra, void* const* ws,
+                                    const size_t* ws_bytes, gridspt_multi* out) {
+    g_err[0] = 0;
+    if (!plans || count < 1 || !delta1_k || !spectra || !ws || !ws_bytes || !out)
+        return fail(GRIDSPT_E_INVALID, "NULL argument or count < 1");
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        const gridspt_plan_s* p = plans[i];
+        if (!p) return fail(GRIDSPT_E_INVALID, "plans[%d] is NULL", i);
+        if (p->d.form != GRIDSPT_FORM_NINE_TERM)
+            return fail(GRIDSPT_E_UNSUPPORTED, "plans[%d]: the work queue runs the nine-term form only", i);
+        if (!queue_supported_n(p->geo.N))
+            return fail(GRIDSPT_E_UNSUPPORTED, "plans[%d]: N=%d; the work queue supports N = 64, 96, 128, 192, 256",
+                        i, p->geo.N);
+        if (p->device != plans[0]->device) return fail(GRIDSPT_E_INVALID, "plans on different devices");
+        for (int j = 0; j < i; ++j)
+            if (ws[j] && ws[j] == ws[i]) return fail(GRIDSPT_E_INVALID, "plans %d and %d share a workspace", j, i);
+    }
+    // record every launch of each plan's run_orders as a stage (its chain)
+    std::vector<std::vector<QStage>> chains(count);
+    for (int i = 0; i < count; ++i) {
+        t_queue = &chains[i];
+        const gridspt_status st = run_orders_impl(plans[i], delta1_k[i], start_order ? start_order[i] : 2,
+                                                  spectra[i], ws[i], ws_bytes[i], nullptr);
+        t_queue = nullptr;
+        if (st != GRIDSPT_OK) return st;
+    }
+    // interleave the chains by cumulative work: the next stage comes from the
+    // chain that has been given the least work so far
+    std::vector<QStage> q;
+    std::vector<size_t> pos(count, 0);
+    std::vector<int> last(count, -1);
+    std::vector<double> cum(count, 0.0);
+    for (;;) {
+        int best = -1;
+        for (int i = 0; i < count; ++i)
+            if (pos[i] < chains[i].size() && (best < 0 || cum[i] < cum[best])) best = i;
+        if (best < 0) break;
+        QStage s = chains[best][pos[best]++];
+        s.dep = last[best];
+        last[best] = (int)q.size();
+        cum[best] += s.cost > 0 ? s.cost : 1.0;
+        q.push_back(s);
+    }
+    const int nst = (int)q.size();
+    std::vector<long long> starts(nst + 1, 0);
+    for (int i = 0; i < nst; ++i) {
+        q[i].tile0 = starts[i];
+        starts[i + 1] = starts[i] + q[i].ntiles;
+    }
+    if (fault_inject("queue_stall") && nst > 1) q[nst / 2].nosignal = 1;
+    gridspt_multi m = new (std::nothrow) gridspt_multi_s();
+    if (!m) return fail(GRIDSPT_E_NOMEM, "host allocation failed");
+    m->nst = nst;
+    m->total = starts[nst];
+    m->status = plans[0]->status;
+    m->device = plans[0]->device;
+    const size_t b_st = align256(sizeof(QStage) * (size_t)nst);
+    const size_t b_so = align256(sizeof(long long) * (size_t)(nst + 1));
+    const size_t b_hd = align256(sizeof(int) * (size_t)(4 + nst));
+    if (gridspt_status st = set_device(plans[0])) { delete m; return st; }
+    cudaError_t e = cudaMalloc(&m->dev, b_st + b_so + b_hd);
+    if (e != cudaSuccess) {
+        delete m;
+        return fail(GRIDSPT_E_NOMEM, "work queue: %s", cudaGetErrorString(e));
+    }
+    char* base = static_cast<char*>(m->dev);
+    m->stages = reinterpret_cast<QStage*>(base);
+    m->starts = reinterpret_cast<long long*>(base + b_st);
+    m->hdr = reinterpret_cast<int*>(base + b_st + b_so);
+    e = cudaMemcpy(m->stages, q.data(), sizeof(QStage) * (size_t)nst, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->starts, starts.data(), sizeof(long long) * (size_t)(nst + 1),
+                                         cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->dev);
+        delete m;
+        return cuda_fail(e, "work queue upload");
+    }
+    *out = m;
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_run_orders_multi(gridspt_multi m, gridspt_stream stream) {
+    g_err[0] = 0;
+    if (!m || !m->dev) return fail(GRIDSPT_E_INVALID, "multi is NULL");
+    int cur = -1;
+    CK(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != m->device) CK(cudaSetDevice(m->device), "cudaSetDevice");
+    double bytes = 0.0;
+    if (g_prof.on) {   // the algorithmic bytes of every stage, counted once per launch
+        static thread_local std::vector<QStage> host;
+        host.resize((size_t)m->nst);
+        CK(cudaMemcpy(host.data(), m->stages, sizeof(QStage) * (size_t)m->nst, cudaMemcpyDeviceToHost),
+           "work queue read-back");
+        for (const QStage& q : host) bytes += q.cost;
+    }
+    CKP(PK_QUEUE, bytes, (cudaStream_t)stream,
+        launch_queue(m->stages, m->starts, m->nst, m->total, m->hdr, m->status, kQueueWaitNs, (cudaStream_t)stream),
+        "work-queue launch");
+    return GRIDSPT_OK;
+}
+
+gridspt_status gridspt_multi_destroy(gridspt_multi m) {
+    if (!m) return GRIDSPT_OK;
+    cudaError_t e = cudaSuccess;
+    if (m->dev) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(m->device);
+        e = cudaDeviceSynchronize();
+        cudaError_t e2 = cudaFree(m->dev);
+        if (e == cudaSuccess) e = e2;
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    delete m;
+    if (e != cudaSuccess) return cuda_fail(e, "multi destroy");
     return GRIDSPT_OK;
 }
 
@@ -1128,8 +1328,11 @@ gridspt_status gridspt_check(gridspt_plan p, gridspt_stream stream) {
     CK(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost), "check: read status");
     if (st) {
         CK(cudaMemset(p->status, 0, sizeof(int)), "check: reset status");
-        return fail(GRIDSPT_E_TIMEOUT, "a bounded device-side wait gave up (status %d); results of the calls since "
-                                       "the last check are invalid", st);
+        if (st & (kStatusWaitTma | kStatusWaitSelftest | kStatusWaitQueue))
+            return fail(GRIDSPT_E_TIMEOUT, "a bounded device-side wait gave up (status %d); results of the calls "
+                                           "since the last check are invalid", st);
+        return fail(GRIDSPT_E_NUMERIC, "an estimator produced a NaN or infinite result since the last check "
+                                       "(status %d): an input spectrum holds non-finite values", st);
     }
     return GRIDSPT_OK;
 }
@@ -1284,8 +1487,15 @@ gridspt_status make_bins(const gridspt_plan_s* p, int nbins, const double* edges
     for (int i = 0; i < nbins; ++i)
         if (!(edges[i] < edges[i + 1]) || !(edges[i] >= 0.0))
             return fail(GRIDSPT_E_INVALID, "edges must be non-negative and increasing");
+    if (!std::isfinite(edges[nbins])) return fail(GRIDSPT_E_INVALID, "edges must be finite");
     bs->nbins = nbins;
-    for (int i = 0; i <= nbins; ++i) bs->thr[i] = (int)s2_threshold(edges[i], p->geo.kF);
+    // thresholds above every mode of the grid (3 (N/2)^2) are clamped there: the
+    // callers reject a last edge above the Nyquist wavenumber
+    const long long cap = 3LL * (p->geo.N / 2) * (p->geo.N / 2) + 1;
+    for (int i = 0; i <= nbins; ++i) {
+        const double r = edges[i] / p->geo.kF;
+        bs->thr[i] = r * r >= (double)cap ? (int)cap : (int)s2_threshold(edges[i], p->geo.kF);
+    }
     (void)kmax;
     return GRIDSPT_OK;
 }
@@ -1322,9 +1532,6 @@ gridspt_status gridspt_power(gridspt_plan p, const void* a_k, const void* b_k, i
 
 }  // extern "C"
 
-namespace {
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-}
 
 extern "C" {
 
@@ -1415,13 +1622,13 @@ gridspt_status gridspt_power_noalloc(gridspt_plan p, const void* a_k, const void
     if (check_plan(p)) return GRIDSPT_E_INVALID;
     if (!a_k || !b_k || !p_out) return fail(GRIDSPT_E_INVALID, "NULL argument");
     if (!aligned16(a_k) || !aligned16(b_k)) return fail(GRIDSPT_E_INVALID, "pointers must be 16-byte aligned");
-    if (!power_static_fits(p->geo, nbins))
-        return fail(GRIDSPT_E_INVALID, "nbins=%d exceeds the %zu-byte static scratch (at most %d bins)", nbins,
-                    power_static_scratch_bytes(), kMaxBins);
     BinSpec bs{};
     if (gridspt_status st = make_bins(p, nbins, edges, 0, &bs)) return st;
     const long long half = p->geo.N / 2;
     if (bs.thr[nbins] > half * half) return fail(GRIDSPT_E_INVALID, "last edge above the Nyquist wavenumber");
+    if (!power_static_fits(p->geo, nbins))
+        return fail(GRIDSPT_E_INVALID, "%d blocks x %d bins of partial sums exceed the %zu-byte static scratch",
+                    power_blocks(p->geo), nbins, power_static_scratch_bytes());
     if (gridspt_status st = set_device(p)) return st;
     double* scratch = nullptr;
     CK(power_static_scratch(&scratch), "static scratch address");

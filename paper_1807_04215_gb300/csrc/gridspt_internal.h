@@ -8,6 +8,19 @@ namespace gridspt {
 
 constexpr int kMaxBins = 64;
 constexpr int kMaxOrder = 8;
+// Blocks of the power estimator's first kernel (one warp per (kx, ky) row,
+// grid-stride): power_blocks() never exceeds this, and the allocation-free
+// entry point's static scratch is sized by it.
+constexpr int kPowerMaxBlocks = 1216;
+
+// Bits of the plan's device status word (read and cleared by gridspt_check).
+constexpr int kStatusWaitTma = 1;       // a bounded mbarrier wait of a TMA-staged pass gave up
+constexpr int kStatusWaitSelftest = 2;  // the bounded-wait self-test's wait gave up
+constexpr int kStatusNonFinite = 4;     // an estimator produced a NaN or infinite result
+
+// Shell-sum accumulation of the estimators (gridspt_desc.accum).
+constexpr int kAccumCompensated = 0;    // FP32 sums with carried rounding error, finished in FP64
+constexpr int kAccumFp64 = 1;           // every term added in FP64
 constexpr int kMaxDeriveOut = 17;
 
 // Grid geometry shared by every launch. Half spectra are float2[N][N][M],
@@ -21,7 +34,8 @@ struct Geo {
     double kF;              // 2 pi / L
     const float2* tw;       // device table e^{+2 pi i j / N}, j < N (FP32 from FP64)
     int var[TV_COUNT];      // tile variant per transform pass
-    int* status;            // device status word: set to 1 when a bounded wait gives up
+    int* status;            // device status word (kStatus* bits)
+    int accum;              // estimator shell sums: kAccumCompensated or kAccumFp64
 };
 
 // number of tile variants per pass (the autotuner times each; results are
@@ -63,6 +77,8 @@ struct XExpArgs {
     int fwd_first;         // 1: inputs hold [x][ky][kz] data; transform forward along x,
                            //    finalise (zero Nyquist, optional cut) and store back in place
     long long s2_nl;       // finalise: zero modes with |s|^2 > s2_nl (< 0: no cut)
+    int zero_k0;           // finalise: also write the k = 0 mode as zero (orders n >= 2,
+                           //    whose k = 0 mode vanishes exactly: mass conservation)
     long long shell_lo;    // XK_SHELL: 0 < |s|^2, lo <= |s|^2 < hi
     long long shell_hi;
     int band;              // > 0: only columns with |ky| < band and kz < band are
@@ -161,8 +177,8 @@ cudaError_t launch_xexp(const Geo& g, const XExpArgs& a, cudaStream_t s);
 cudaError_t launch_yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);
 cudaError_t launch_zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);
 // Forward column transform along x (axis 0) or y (axis 1) of `count` fields,
-// in place. finalize (x axis): zero Nyquist modes and |s|^2 > s2_nl (s2_nl < 0:
-// no cut).
+// in place. finalize (x axis): 1 zeroes the Nyquist modes and |s|^2 > s2_nl
+// (s2_nl < 0: no cut); 2 also the k = 0 mode (orders n >= 2 of the recursion).
 cudaError_t launch_colpass_fwd(const Geo& g, float2* data, long long fstride, int count, int axis,
                                int finalize, long long s2_nl, cudaStream_t s);
 // Contiguous-axis real-to-complex with output scale.
@@ -240,6 +256,64 @@ cudaError_t launch_mlp_mse(const float* y, const float* t, const float* mask, lo
 cudaError_t launch_mlp_adam(float* master, void* lowp, int bf16, const float* grad, float* m, float* v, int* step,
                             long long n, float lr, float b1, float b2, float eps, cudaStream_t s);
 cudaError_t launch_mlp_convert(const float* src, void* dst, int bf16, long long n, cudaStream_t s);
+
+// ------------------------------------------------ persistent work queue
+// The recursion of several plans (grid sizes may differ) as one launch of a
+// persistent kernel (k_persistent.cu): every launch that gridspt_run_orders
+// would make becomes a stage of tiles in a device-side queue, stages of one
+// plan form a chain (each waits for its predecessor), chains of different
+// plans are interleaved by their cumulative work. Blocks take tiles in queue
+// order from a ticket counter; a tile first waits (bounded) for its stage's
+// predecessor to complete, runs, and counts itself done.
+enum QKind : int {
+    Q_XEXP0 = 0,   // x expansion, backward only (x)
+    Q_XEXP1,       // x expansion, forward first (x)
+    Q_YEXP,        // y expansion (y)
+    Q_Z,           // z expansion, store only or fused pair products (z)
+    Q_ZR2C,        // contiguous-axis forward transform (r2c: data, count, scale)
+    Q_COLY,        // forward column pass along y (data, count)
+    Q_COLX,        // forward column pass along x with finalise (data, count, s2, zero_k0)
+    Q_PRODUCT,     // diagonal pair (pr)
+    Q_ZEROBAND,    // zeros outside the band columns (data, data2, band)
+    Q_KINDS
+};
+constexpr int kQueueThreads = 256;
+constexpr int kStatusWaitQueue = 8;     // a work-queue tile's wait for its predecessor gave up
+struct QStage {
+    int kind;
+    int N;
+    int dep;               // stage this one waits for (-1: none)
+    int nosignal;          // fault injection: this stage never counts its tiles done
+    long long ntiles;
+    long long tile0;       // first ticket of the stage
+    int gx, gy;            // virtual grid of the column passes (tile = bx + gx (by + gy bz))
+    int count;             // fields of Q_ZR2C / Q_COLY / Q_COLX
+    int zero_k0;           // Q_COLX
+    int band;              // Q_ZEROBAND
+    long long s2;          // Q_COLX: s2_nl
+    float scale;           // Q_ZR2C
+    float kF, inv_kF2;
+    const float2* tw;
+    float2* data;          // Q_ZR2C (in place), Q_COLY, Q_COLX, Q_ZEROBAND (first field)
+    float2* data2;         // Q_ZEROBAND (second field)
+    long long fstride;
+    double cost;           // work estimate (algorithmic bytes), host only
+    XExpArgs x;
+    YZExpArgs y;
+    ZPairArgs z;
+    ProductArgs pr;
+};
+// Supported grid sizes of the queue kernel (its tile bodies are instantiated
+// for these); false for the others.
+bool queue_supported_n(int N);
+// Tiles of a stage whose kind, N and arguments are set (fills gx, gy, ntiles).
+void queue_tiles(QStage& st);
+// Launch over `nst` stages already in device memory (stages, starts[nst + 1]
+// first tickets with starts[nst] = total), with hdr (2 + nst ints, zeroed by
+// this call on `s`): ticket counter, abort flag, per-stage done counters.
+cudaError_t launch_queue(const QStage* stages, const long long* starts, int nst, long long total, int* hdr,
+                         int* status, long long wait_ns, cudaStream_t s);
+size_t queue_smem_bytes();
 
 // Library-owned scratch of the allocation-free power entry point
 // (k_power_static.cu): device address of the static array on the current

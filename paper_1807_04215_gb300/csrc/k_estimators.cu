@@ -16,7 +16,11 @@
 // The scan runs in FP32 with each addition's rounding error carried exactly
 // (Knuth's two-sum) and added at the tail, so a run's sum is good to about
 // FP32^2 while the FP64 pipe (a small fraction of the FP32 rate here) sees
-// one addition per run; the mode counts are exact in FP32.
+// one addition per run; the mode counts are exact in FP32. With the FP64
+// accumulator choice (Geo::accum = kAccumFp64) every product is formed and
+// scanned in FP64 instead (the FP32 inputs' products are exact in FP64).
+// The final kernels flag a NaN or infinite result in the plan's status word
+// (kStatusNonFinite), which gridspt_check reports as GRIDSPT_E_NUMERIC.
 //
 // Bispectrum (Eq. bk_tree, FFT shell estimator): the per-shell sums are formed
 // in k_zshell (k_transform.cuh); the final fixed-order reduction is here.
@@ -29,9 +33,40 @@ constexpr int kPowWarps = 8;
 int power_blocks(const Geo& g) {
     const long long rows = (long long)g.N * g.N;
     long long b = (rows + kPowWarps - 1) / kPowWarps;
-    return (int)(b < 1216 ? b : 1216);
+    return (int)(b < kPowerMaxBlocks ? b : kPowerMaxBlocks);
 }
 
+// Segmented inclusive scan over runs of equal bin within a warp; T = float
+// (two-sum compensated, error carried in e) or double (plain FP64 adds, e
+// unused). The scan's shuffles and the run boundaries are the same for both.
+template <typename T>
+__device__ __forceinline__ void seg_scan(T (&v)[2], T (&e)[2], float (&c)[2], const int (&bin)[2], int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const T ov = __shfl_up_sync(0xffffffffu, v[h], off);
+            T oe = T(0);
+            if constexpr (sizeof(T) == 4) oe = __shfl_up_sync(0xffffffffu, e[h], off);
+            const float oc = __shfl_up_sync(0xffffffffu, c[h], off);
+            const int ob = __shfl_up_sync(0xffffffffu, bin[h], off);
+            if (lane >= off && ob == bin[h]) {
+                if constexpr (sizeof(T) == 4) {
+                    const float t = __fadd_rn(v[h], ov);         // two-sum: t + r = v + ov exactly
+                    const float bv = __fsub_rn(t, v[h]);
+                    const float r = __fadd_rn(__fsub_rn(v[h], __fsub_rn(t, bv)), __fsub_rn(ov, bv));
+                    v[h] = t;
+                    e[h] = __fadd_rn(__fadd_rn(e[h], oe), r);
+                } else {
+                    v[h] = v[h] + ov;
+                }
+                c[h] += oc;
+            }
+        }
+    }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kPowWarps * 32)
 k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins, int N, int M,
         double* __restrict__ partial) {
@@ -57,7 +92,8 @@ k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins
         // (latency hiding); their sums reach acc in chunk order, as one at a time
         for (int kz0 = 0; kz0 < M; kz0 += 64) {
             if (sxy + kz0 * kz0 >= top) break;
-            float v[2], e[2], c[2];              // sum, carried rounding error, weight
+            T v[2], e[2];                        // sum, carried rounding error (FP32 only)
+            float c[2];                          // weight (mode count)
             int bin[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -75,35 +111,20 @@ k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins
                     }
                     bin[h] = lo;
                 }
-                v[h] = 0.f;
-                e[h] = 0.f;
+                v[h] = T(0);
+                e[h] = T(0);
                 c[h] = 0.f;
                 if (bin[h] >= 0 && bin[h] < nb) {
                     const float2 x = ar[kz], y = br[kz];
                     const float wgt = kz == 0 ? 1.f : 2.f;
-                    v[h] = wgt * fmaf(x.x, y.x, x.y * y.y);
+                    if constexpr (sizeof(T) == 4)
+                        v[h] = wgt * fmaf(x.x, y.x, x.y * y.y);
+                    else
+                        v[h] = (double)wgt * ((double)x.x * (double)y.x + (double)x.y * (double)y.y);
                     c[h] = wgt;
                 }
             }
-            // segmented inclusive scans over runs of equal bin
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float ov = __shfl_up_sync(0xffffffffu, v[h], off);
-                    const float oe = __shfl_up_sync(0xffffffffu, e[h], off);
-                    const float oc = __shfl_up_sync(0xffffffffu, c[h], off);
-                    const int ob = __shfl_up_sync(0xffffffffu, bin[h], off);
-                    if (lane >= off && ob == bin[h]) {
-                        const float t = __fadd_rn(v[h], ov);         // two-sum: t + r = v + ov exactly
-                        const float bv = __fsub_rn(t, v[h]);
-                        const float r = __fadd_rn(__fsub_rn(v[h], __fsub_rn(t, bv)), __fsub_rn(ov, bv));
-                        v[h] = t;
-                        e[h] = __fadd_rn(__fadd_rn(e[h], oe), r);
-                        c[h] += oc;
-                    }
-                }
-            }
+            seg_scan<T>(v, e, c, bin, lane);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int nxt = __shfl_down_sync(0xffffffffu, bin[h], 1);
@@ -132,7 +153,7 @@ k_power(const float2* __restrict__ a, const float2* __restrict__ b, BinSpec bins
 // fixed shared-memory tree; bitwise repeatable.
 __global__ void __launch_bounds__(256)
 k_power_final(const double* __restrict__ partial, int G, int nb, double vol,
-              double* __restrict__ p_out, int64_t* __restrict__ nk_out) {
+              double* __restrict__ p_out, int64_t* __restrict__ nk_out, int* __restrict__ status) {
     __shared__ double rs[256], rc[256];
     const int t = blockIdx.x;
     double s = 0.0, c = 0.0;
@@ -151,8 +172,10 @@ k_power_final(const double* __restrict__ partial, int G, int nb, double vol,
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        p_out[t] = rc[0] > 0.0 ? vol * rs[0] / rc[0] : 0.0;
+        const double pv = rc[0] > 0.0 ? vol * rs[0] / rc[0] : 0.0;
+        p_out[t] = pv;
         if (nk_out) nk_out[t] = (int64_t)(rc[0] + 0.5);
+        if (!isfinite(pv)) atomicOr(status, kStatusNonFinite);
     }
 }
 
@@ -160,10 +183,13 @@ cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const B
                          double* partial, double* p_out, int64_t* nk_out, double volume,
                          cudaStream_t s) {
     const int G = power_blocks(g);
-    k_power<<<G, kPowWarps * 32, 0, s>>>(a, b, bins, g.N, g.M, partial);
+    if (g.accum == kAccumFp64)
+        k_power<double><<<G, kPowWarps * 32, 0, s>>>(a, b, bins, g.N, g.M, partial);
+    else
+        k_power<float><<<G, kPowWarps * 32, 0, s>>>(a, b, bins, g.N, g.M, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_power_final<<<bins.nbins, 256, 0, s>>>(partial, G, bins.nbins, volume, p_out, nk_out);
+    k_power_final<<<bins.nbins, 256, 0, s>>>(partial, G, bins.nbins, volume, p_out, nk_out, g.status);
     return cudaGetLastError();
 }
 
@@ -172,7 +198,7 @@ cudaError_t launch_power(const Geo& g, const float2* a, const float2* b, const B
 // E = L^6 sum I_a^2 I_b / sum J^3, N_tri = sum J^3 / N^3; one block, fixed order.
 __global__ void __launch_bounds__(256)
 k_bispec_final(const double* __restrict__ partial, int G, int nfields, double* __restrict__ j3_cache, double vol2,
-               double cells, double* __restrict__ e_out, double* __restrict__ ntri_out) {
+               double cells, double* __restrict__ e_out, double* __restrict__ ntri_out, int* __restrict__ status) {
     __shared__ double r1[256], r2[256];
     double s1 = 0.0, s2 = 0.0;
     for (int g = threadIdx.x; g < G; g += 256) {
@@ -194,15 +220,17 @@ k_bispec_final(const double* __restrict__ partial, int G, int nfields, double* _
         if (nfields == 3) *j3_cache = j3;
         else j3 = *j3_cache;
         const double nt = j3 / cells;
+        const double ev = nt > 0.5 ? vol2 * r1[0] / j3 : 0.0;
         *ntri_out = nt;
-        *e_out = nt > 0.5 ? vol2 * r1[0] / j3 : 0.0;
+        *e_out = ev;
+        if (!isfinite(ev) || !isfinite(nt) || !isfinite(r1[0])) atomicOr(status, kStatusNonFinite);
     }
 }
 
 cudaError_t launch_bispec_final(const Geo& g, const double* partial, int blocks, int nfields, double* j3_cache,
                                 double* e_out, double* ntri_out, double vol2, cudaStream_t s) {
     k_bispec_final<<<1, 256, 0, s>>>(partial, blocks, nfields, j3_cache, vol2, (double)g.N * g.N * g.N, e_out,
-                                     ntri_out);
+                                     ntri_out, g.status);
     return cudaGetLastError();
 }
 

@@ -20,18 +20,18 @@ namespace gridspt {
 
 namespace {
 
-constexpr int kStaticMaxBlocks = 1216;   // power_blocks() never exceeds this
 constexpr int kMaxDevices = 64;
 
-// 1216 blocks x 2 sums x 64 bins x 8 bytes = 1,245,184 bytes per device.
-static __device__ __align__(256) double g_power_scratch[(size_t)kStaticMaxBlocks * 2 * kMaxBins];
+// kPowerMaxBlocks (1216) blocks x 2 sums x 64 bins x 8 bytes = 1,245,184 bytes per device.
+static __device__ __align__(256) double g_power_scratch[(size_t)kPowerMaxBlocks * 2 * kMaxBins];
+static_assert(sizeof(g_power_scratch) == (size_t)1245184, "static scratch size stated in gridspt.h");
 
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
 
 }  // namespace
 
-size_t power_static_scratch_bytes() { return sizeof(double) * (size_t)kStaticMaxBlocks * 2 * kMaxBins; }
+size_t power_static_scratch_bytes() { return sizeof(g_power_scratch); }
 
 cudaError_t power_static_scratch(double** out) {
     int dev = -1;
@@ -50,7 +50,7 @@ cudaError_t power_static_scratch(double** out) {
 }
 
 bool power_static_fits(const Geo& g, int nbins) {
-    return nbins >= 1 && nbins <= kMaxBins && power_blocks(g) <= kStaticMaxBlocks;
+    return (size_t)power_blocks(g) * 2 * nbins * sizeof(double) <= sizeof(g_power_scratch);
 }
 
 }  // namespace gridspt

@@ -21,7 +21,7 @@ __global__ void k_wait_selftest(int* status) {
         done = d != 0;
         __nanosleep(64);
     }
-    if (!done && threadIdx.x == 0) atomicExch(status, 2);
+    if (!done && threadIdx.x == 0) atomicOr(status, kStatusWaitSelftest);
 }
 
 cudaError_t launch_wait_selftest(int* status, cudaStream_t s) {

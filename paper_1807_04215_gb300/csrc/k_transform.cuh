@@ -133,22 +133,25 @@ __device__ __forceinline__ void tile_store(float2* dst, const float2* tile, long
 }
 
 // ------------------------------------------------- forward column pass
+// The pass bodies below take their block coordinates (bx, by, bz) and shared
+// memory explicitly, so that the same code runs as a kernel of its own (block
+// coordinates from blockIdx) and as a tile of the persistent work-queue kernel
+// (k_persistent.cu); the block has TZ * P threads either way.
 template <int N, int TZ, int AXIS, bool FIN>
-__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
-k_colpass(float2* __restrict__ data, long long fstride, const float2* __restrict__ twg,
-          long long s2_nl) {
+__device__ __forceinline__ void colpass_body(float2* __restrict__ data, long long fstride,
+                                             const float2* __restrict__ twg, long long s2_nl, int zero_k0,
+                                             int bx, int by, int bz, float2* sm) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
-    extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* buf = sm + N;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
-    const int kz = blockIdx.x * TZ + c;
-    const int a = blockIdx.y;
+    const int kz = bx * TZ + c;
+    const int a = by;
     const bool act = kz < M;
     constexpr long long estride = AXIS == 0 ? (long long)N * M : (long long)M;
     constexpr long long astride = AXIS == 0 ? (long long)M : (long long)N * M;
-    float2* col = data + blockIdx.z * fstride + a * astride + kz;
+    float2* col = data + bz * fstride + a * astride + kz;
     float2 x[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) x[i] = act ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
@@ -161,13 +164,22 @@ k_colpass(float2* __restrict__ data, long long fstride, const float2* __restrict
             const int n = p + P * i;
             const int sx = signed_idx(n, N);
             const long long s2 = (long long)sx * sx + (long long)sy * sy + (long long)sz * sz;
-            if (n == N / 2 || a == N / 2 || (s2_nl >= 0 && s2 > s2_nl)) x[i] = make_float2(0.f, 0.f);
+            if (n == N / 2 || a == N / 2 || (s2_nl >= 0 && s2 > s2_nl) || (zero_k0 && s2 == 0))
+                x[i] = make_float2(0.f, 0.f);
         }
     }
     if (act) {
 #pragma unroll
         for (int i = 0; i < E; ++i) col[(p + P * i) * estride] = x[i];
     }
+}
+
+template <int N, int TZ, int AXIS, bool FIN>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
+k_colpass(float2* __restrict__ data, long long fstride, const float2* __restrict__ twg,
+          long long s2_nl, int zero_k0) {
+    extern __shared__ float2 sm[];
+    colpass_body<N, TZ, AXIS, FIN>(data, fstride, twg, s2_nl, zero_k0, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
 // ------------------------------------------------ contiguous axis: R2C
@@ -235,17 +247,15 @@ __host__ __device__ constexpr int xexp_min_blocks() {
 // A = i k . V, B = -(k^2 / 2) S, delta = cdA A + cdB B, theta = ctA A + ctB B
 // (written to src0, src1 and finalised like MODE 1).
 template <int N, int TZ, int MODE>
-__global__ void __launch_bounds__(TZ * Cfg<N>::PC, xexp_min_blocks<N, TZ, MODE>())
-k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
+__device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __restrict__ twg, float kF,
+                                          float inv_kF2, int bx, int by, float2* sm) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
-    extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* buf = sm + N;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
-    const int kz = blockIdx.x * TZ + c;
+    const int kz = bx * TZ + c;
     const int B = args.band;
-    const int by = blockIdx.y;
     const int ky = (B > 0 && by >= B) ? N - (2 * B - 1 - by) : by;   // band rows: [0, B) and (N - B, N)
     const bool act = kz < M && (B <= 0 || kz < B);
     constexpr long long estride = (long long)N * M;
@@ -304,7 +314,7 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
             const int n = p + P * i;
             const int sx = signed_idx(n, N);
             const long long s2 = (long long)sx * sx + syz;
-            if (n == N / 2 || ky == N / 2 || (args.s2_nl >= 0 && s2 > args.s2_nl)) {
+            if (n == N / 2 || ky == N / 2 || (args.s2_nl >= 0 && s2 > args.s2_nl) || (args.zero_k0 && s2 == 0)) {
                 xd[i] = make_float2(0.f, 0.f);
                 xt[i] = make_float2(0.f, 0.f);
             }
@@ -357,6 +367,13 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
     }
 }
 
+template <int N, int TZ, int MODE>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC, xexp_min_blocks<N, TZ, MODE>())
+k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
+    extern __shared__ float2 sm[];
+    xexp_body<N, TZ, MODE>(args, twg, kF, inv_kF2, blockIdx.x, blockIdx.y, sm);
+}
+
 // ------------------------------------------------------------ y expansion
 // Output f = ky^b * x-field[in], transformed backward along y. Outputs of one
 // input are consecutive; the input column is loaded once and kept in
@@ -367,17 +384,16 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
 // cp.async (8-byte, zero-filled where the band excludes it) while the outputs
 // of the current input are transformed.
 template <int N, int TZ, bool PF>
-__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
-k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+__device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* __restrict__ twg, float kF, int bx,
+                                          int by, float2* sm) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
-    extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* buf = sm + N;
     float2* pre = buf + N * TZ;                  // PF: next input tile, element (n, c) at n * TZ + c
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
     load_table(tw, twg, N);
-    const int kz = blockIdx.x * TZ + c;
-    const int xr = blockIdx.y;
+    const int kz = bx * TZ + c;
+    const int xr = by;
     const int B = args.band;
     const bool act = kz < M && (B <= 0 || kz < B);
     constexpr long long estride = (long long)M;
@@ -436,6 +452,13 @@ k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
             for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
         }
     }
+}
+
+template <int N, int TZ, bool PF>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
+k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+    extern __shared__ float2 sm[];
+    yexp_body<N, TZ, PF>(args, twg, kF, blockIdx.x, blockIdx.y, sm);
 }
 
 // Column-pair form of k_yexp: each thread holds two adjacent kz columns, so
@@ -1077,7 +1100,7 @@ k_yexp_tma(YZExpArgs args, const __grid_constant__ CUtensorMap tmap, const float
     // never leave with a copy in flight into this block's shared memory
     for (int b = 0; b < 2; ++b)
         if (pending[b]) ok = mbar_wait(&bar[b], phase[b]) && ok;
-    if (!ok && tid == 0) atomicExch(status, 1);
+    if (!ok && tid == 0) atomicOr(status, kStatusWaitTma);
 }
 
 // ------------------------------------------- z pass fused with the shell sums
@@ -1085,7 +1108,9 @@ k_yexp_tma(YZExpArgs args, const __grid_constant__ CUtensorMap tmap, const float
 // estimator): the three xy-fields I_a, I_b, J (nonzero only for kz < band)
 // are transformed to real rows in shared memory; every thread then holds the
 // same cells of all three rows, forms I_a^2 I_b and J^3 in FP32 and keeps
-// Kahan-compensated FP32 sums; the block writes FP64 partials (fixed order).
+// Kahan-compensated FP32 sums (FP64 sums of the same terms, in the same order,
+// with the FP64 accumulator choice, f64 = 1); the block writes FP64 partials
+// (fixed order).
 __device__ __forceinline__ void kahan_add2(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -1105,7 +1130,7 @@ __device__ __forceinline__ float cell_mul3(float2 a, float2 b, float2 c) {
 template <int N, int TZ, int NF, bool TRI>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ, (TZ * Cfg<N>::PZ <= 512) ? 2 : 1)
 k_zshell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
-         double* __restrict__ partial) {
+         double* __restrict__ partial, int f64) {
     constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH, NT = TZ * P;
     extern __shared__ float2 sm[];
     float2* tw = sm;
@@ -1167,7 +1192,15 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
     __syncthreads();
     if (tid < 32) {
         float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+        double d1 = 0.0, d2 = 0.0;                     // FP64 accumulator choice (f64)
         auto chain = [&](int cc, int pp) {
+            if (f64) {
+                for (int i = 0; i < E; ++i) {
+                    d1 += (double)T1[(cc * P + pp) * E + i];
+                    if constexpr (NF > ND) d2 += (double)T2[(cc * P + pp) * E + i];
+                }
+                return;
+            }
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 kahan_add2(s1, c1, T1[(cc * P + pp) * E + i]);
@@ -1181,7 +1214,7 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
             for (int cc = 0; cc < TZ; ++cc)
                 for (int pp = tid; pp < P; pp += 32) chain(cc, pp);
         }
-        double a = (double)s1 - (double)c1, b = (double)s2 - (double)c2;
+        double a = f64 ? d1 : (double)s1 - (double)c1, b = f64 ? d2 : (double)s2 - (double)c2;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, off);
@@ -1206,7 +1239,7 @@ k_zshell(const float2* __restrict__ in, long long in_stride, int band, const flo
 template <int N, int NF, bool TRI>
 __global__ void __launch_bounds__(kRowWarps * 32, 2)
 k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const float2* __restrict__ twg,
-             double* __restrict__ partial) {
+             double* __restrict__ partial, int f64) {
     using C = RowCfg<N>;
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW;
     constexpr int G = Cfg<N>::TZZ0;
@@ -1223,6 +1256,7 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
     for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups;
          grp += (long long)gridDim.x * kRowWarps) {
         float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;   // this lane's chains over its rows
+        double d1 = 0.0, d2 = 0.0;                      // FP64 accumulator choice (f64)
         for (int rr = 0; rr < G; rr += RW) {
             const long long row = grp * G + rr + r;
             // one band-limited row of field f, packed and transformed to real cells
@@ -1245,17 +1279,28 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
                 float2 x[ND][E];
 #pragma unroll
                 for (int f = 0; f < ND; ++f) real_row(f, x[f]);
+                if (f64) {
 #pragma unroll
-                for (int i = 0; i < E; ++i) kahan_add2(s1, c1, cell_mul3(x[0][i], x[TRI ? 1 : 0][i], x[ND - 1][i]));
+                    for (int i = 0; i < E; ++i) d1 += (double)cell_mul3(x[0][i], x[TRI ? 1 : 0][i], x[ND - 1][i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < E; ++i)
+                        kahan_add2(s1, c1, cell_mul3(x[0][i], x[TRI ? 1 : 0][i], x[ND - 1][i]));
+                }
             }
             if constexpr (NF > ND) {                      // J after the data fields: fewer live registers
                 float2 xj[E];
                 real_row(NF - 1, xj);
+                if (f64) {
 #pragma unroll
-                for (int i = 0; i < E; ++i) kahan_add2(s2, c2, cell_mul3(xj[i], xj[i], xj[i]));
+                    for (int i = 0; i < E; ++i) d2 += (double)cell_mul3(xj[i], xj[i], xj[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < E; ++i) kahan_add2(s2, c2, cell_mul3(xj[i], xj[i], xj[i]));
+                }
             }
         }
-        double a = (double)s1 - (double)c1, b = (double)s2 - (double)c2;
+        double a = f64 ? d1 : (double)s1 - (double)c1, b = f64 ? d2 : (double)s2 - (double)c2;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, off);
@@ -1334,7 +1379,7 @@ struct Launch {
 #define GRIDSPT_COL(AX_, FIN_)                                                        \
     e = set_smem(k_colpass<N, TZC, AX_, FIN_>, smem);                                 \
     if (e != cudaSuccess) return e;                                                   \
-    k_colpass<N, TZC, AX_, FIN_><<<grid, TZC * PC, smem, s>>>(d, fs, g.tw, s2_nl);    \
+    k_colpass<N, TZC, AX_, FIN_><<<grid, TZC * PC, smem, s>>>(d, fs, g.tw, s2_nl, fin == 2); \
     return cudaGetLastError();
         if (axis == 0) {
             if (fin) { GRIDSPT_COL(0, true) }
@@ -1515,7 +1560,7 @@ struct Launch {
             const long long need = (groups + kRowWarps - 1) / kRowWarps;
             const long long resident = (long long)(per > 0 ? per : 1) * sms;
             k_zrow_shell<N, NF, TRI><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
-                in, st, band, g.tw, partial);
+                in, st, band, g.tw, partial, g.accum == kAccumFp64);
             return cudaGetLastError();
         }
     }
@@ -1525,7 +1570,8 @@ struct Launch {
         const size_t smem = sizeof(float2) * (N + (size_t)NF * TZZ * PITCH);
         cudaError_t e = set_smem(k_zshell<N, TZZ, NF, TRI>, smem);
         if (e != cudaSuccess) return e;
-        k_zshell<N, TZZ, NF, TRI><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial);
+        k_zshell<N, TZZ, NF, TRI><<<shell_blocks(), TZZ * PZ, smem, s>>>(in, st, band, g.tw, partial,
+                                                                          g.accum == kAccumFp64);
         return cudaGetLastError();
     }
     // nf: data fields (2: a, b; 3 with tri: a, b, c) plus J when present

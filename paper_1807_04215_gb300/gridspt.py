@@ -39,20 +39,27 @@ class Plan:
     """Owns a gridspt_plan (twiddle table on the current device)."""
 
     FORMS = {"nine_term": 0, "divergence": 1}
+    ACCUMS = {"compensated": 0, "fp64": 1}
 
-    def __init__(self, n, n_max, box, batch=1, kcut_lin=0.0, kcut_nl=0.0, form="nine_term", truncate=False):
+    def __init__(self, n, n_max, box, batch=1, kcut_lin=0.0, kcut_nl=0.0, form="nine_term", truncate=False,
+                 accum="compensated"):
         """form: "nine_term" (the paper's bilinear sources) or "divergence"
         (A_n = div sum delta_m u_{n-m}, B_n = lap sum u_m . u_{n-m} / 2; equal in
         band, four real fields per order). truncate: cut every order j >= 2 at
         min(j, n_max + 1 - j) K_c (outputs at |k| <= K_c unchanged; nine-term
-        form only)."""
+        form only). accum: shell sums of the estimators, "compensated" (FP32
+        with carried rounding error, finished in FP64) or "fp64"."""
         self.lib = _lib.load()
         if form not in self.FORMS:
             raise ValueError(f"form must be one of {sorted(self.FORMS)}")
+        if accum not in self.ACCUMS:
+            raise ValueError(f"accum must be one of {sorted(self.ACCUMS)}")
         self.desc = Desc(n, n_max, box, batch, kcut_lin, kcut_nl)
         self.form = form
         self.truncate = bool(truncate)
-        d = _lib.GridsptDesc(n, n_max, batch, self.FORMS[form], box, kcut_lin, kcut_nl, int(bool(truncate)))
+        self.accum = accum
+        d = _lib.GridsptDesc(n, n_max, batch, self.FORMS[form], box, kcut_lin, kcut_nl, int(bool(truncate)),
+                             self.ACCUMS[accum])
         h = ctypes.c_void_p()
         _lib.check("gridspt_plan_create", self.lib.gridspt_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -172,8 +179,54 @@ class Batch:
             pass
 
 
+class Multi:
+    """gridspt_multi: the recursion of several plans (sizes may differ) as one
+    launch of the persistent work-queue kernel (gridspt_run_orders_multi per
+    launch()). Keeps the tensors it was built on alive (the queue holds their
+    addresses)."""
+
+    def __init__(self, plans, delta1s, spectra=None, wss=None, start_orders=None):
+        self.lib = _lib.load()
+        n = len(plans)
+        spectra = list(spectra) if spectra is not None else [
+            torch.empty(p.half_shape(p.batch, p.n_max - 1, 2), dtype=torch.complex64, device="cuda") for p in plans]
+        wss = list(wss) if wss is not None else [
+            torch.empty(max(p.workspace_size(), 16), dtype=torch.uint8, device="cuda") for p in plans]
+        starts = list(start_orders) if start_orders is not None else [2] * n
+        for p, d, sp in zip(plans, delta1s, spectra):
+            p._check_half(d, (p.batch,), "delta1")
+            p._check_half(sp, (p.batch, p.n_max - 1, 2), "spectra")
+        self.keep = (plans, list(delta1s), spectra, wss)
+        arr = lambda T, xs: (T * n)(*xs)  # noqa: E731
+        h = ctypes.c_void_p()
+        _lib.check("gridspt_multi_create", self.lib.gridspt_multi_create(
+            arr(ctypes.c_void_p, [p.handle.value for p in plans]), n,
+            arr(ctypes.c_void_p, [d.data_ptr() for d in delta1s]), arr(ctypes.c_int32, starts),
+            arr(ctypes.c_void_p, [x.data_ptr() for x in spectra]), arr(ctypes.c_void_p, [w.data_ptr() for w in wss]),
+            arr(ctypes.c_size_t, [w.numel() for w in wss]), ctypes.byref(h)))
+        self.handle = h
+        self.spectra = spectra
+
+    def launch(self):
+        _lib.check("gridspt_run_orders_multi", self.lib.gridspt_run_orders_multi(self.handle, _stream()))
+        return self.spectra
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.check("gridspt_multi_destroy", self.lib.gridspt_multi_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def check(plan):
-    """gridspt_check: raises GridsptError (status 5) if a bounded device wait gave up."""
+    """gridspt_check: raises GridsptError with status 5 (GRIDSPT_E_TIMEOUT) if a
+    bounded device wait gave up, 6 (GRIDSPT_E_NUMERIC) if an estimator result
+    was NaN or infinite since the last check."""
     _lib.check("gridspt_check", plan.lib.gridspt_check(plan.handle, _stream()))
 
 

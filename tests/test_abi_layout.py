@@ -15,7 +15,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 STRUCTS = {
-    "gridspt_desc": ("GridsptDesc", ["n", "n_max", "batch", "form", "box", "kcut_lin", "kcut_nl", "truncate"]),
+    "gridspt_desc": ("GridsptDesc", ["n", "n_max", "batch", "form", "box", "kcut_lin", "kcut_nl", "truncate",
+                                     "accum"]),
     "gridspt_cosmo": ("GridsptCosmo", ["omega_m", "h", "n_s", "sigma8", "gamma"]),
     "gridspt_kernel_stat": ("GridsptKernelStat", ["name", "launches", "reserved", "ms", "bytes"]),
 }

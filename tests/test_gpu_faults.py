@@ -86,3 +86,38 @@ def test_bounded_device_wait_reports_timeout_and_context_stays_usable():
     assert torch.equal(g.run_orders(plan, d1), a)
     g.check(plan)
     del ctypes
+
+
+def test_non_finite_estimator_result_is_reported_as_numeric():
+    """A NaN planted in an input spectrum (inside a bin) makes that bin's power
+    NaN; gridspt_check reports GRIDSPT_E_NUMERIC once and resets, and the next
+    call on finite inputs is correct and clean. Same for the bispectrum."""
+    import math
+    N, L = 32, 250.0
+    plan = g.Plan(N, 3, L)
+    d1 = g.make_linear_field(plan, [5])
+    kF = 2 * math.pi / L
+    edges = [kF * (b + 0.5) for b in range(9)]
+    ref, _ = g.power(plan, d1[0], d1[0], edges)
+    ref = ref.clone()
+    g.check(plan)
+    bad = d1[0].clone()
+    bad[3, 0, 0] = complex(float("nan"), 0.0)          # |s| = 3: bin 2
+    p, _ = g.power(plan, bad, bad, edges)
+    assert math.isnan(float(p[2])) and torch.isfinite(p[:2]).all()
+    with pytest.raises(_lib.GridsptError) as ei:
+        g.check(plan)
+    assert ei.value.status == 6                       # GRIDSPT_E_NUMERIC
+    g.check(plan)                                     # reset by the previous check
+    again, _ = g.power(plan, d1[0], d1[0], edges)
+    assert torch.equal(again, ref)
+    g.check(plan)
+    kc = kF * N / 4
+    bed = [kc * i / 4 for i in range(5)]
+    E, _ = g.bispectrum(plan, bad, d1[0], bed)
+    with pytest.raises(_lib.GridsptError) as ei:
+        g.check(plan)
+    assert ei.value.status == 6
+    E, _ = g.bispectrum(plan, d1[0], d1[0], bed)
+    g.check(plan)
+    assert torch.isfinite(E).all()
