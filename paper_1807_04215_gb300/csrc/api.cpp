@@ -156,8 +156,8 @@ QStage q_stage(const Geo& g, int kind, double cost) {
     q.N = g.N;
     q.dep = -1;
     q.tw = g.tw;
-    q.kF = (float)g.kF;
-    q.inv_kF2 = (float)(1.0 / (g.kF * g.kF));
+    q.kF = kDerivUnit;
+    q.inv_kF2 = 1.0f / (kDerivUnit * kDerivUnit);
     q.cost = cost;
     return q;
 }

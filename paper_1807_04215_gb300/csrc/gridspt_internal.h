@@ -48,6 +48,19 @@ struct Geo {
 //   z forward pass: 0, 1 tiles, 2 warp rows.
 constexpr int kTuneVariants[TV_COUNT] = {2, 2, 5, 3, 3};
 
+// Unit of the wavevector in the derivative multipliers of the expansion
+// passes: k_F, i.e. integer wavevectors s. Every source term of Eq.
+// recursion_formula pairs one derivative (i k) with one inverse derivative
+// (-i k / k^2) or none (d_a d_b / nabla^2, delta theta), so k_F cancels from
+// A_n, B_n exactly and the stored derived fields need no physical unit. With
+// integer s the cancellations the sources rely on (grad delta . u + delta
+// theta and the u-tensor terms at k -> 0, mass and momentum conservation) are
+// exact up to the rounding of 1/|s|^2 per mode; a physical k_F would carry
+// the FP32 rounding of k_F^2 * (1 / k_F^2) - 1 coherently into every mode and
+// leave a relative error growing as 1/k^2 in the low-k part of delta_3, which
+// P13 = 2 <delta_1 delta_3> measures.
+constexpr float kDerivUnit = 1.0f;
+
 // Factorised spectral derivatives (Sec. II.C steps (2) and (5)). Every
 // derived field is c * kx^a * ky^b * kz^g * src(k) with src in {delta, theta,
 // phi = theta / k^2} and c in {1, i, -i}. Factors of (ky, kz) commute with the

@@ -1425,7 +1425,7 @@ struct Launch {
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, B ? 2 * B - 1 : N);
         const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
-        const float kF = (float)g.kF, ikF2 = (float)(1.0 / (g.kF * g.kF));
+        const float kF = kDerivUnit, ikF2 = 1.0f / (kDerivUnit * kDerivUnit);
         cudaError_t e;
         if (a.fwd_first && a.div_in) {
             e = set_smem(k_xexp<N, TZC, 2>, smem);
@@ -1448,7 +1448,7 @@ struct Launch {
         const size_t smem = sizeof(float2) * (N + (N & 1) + (size_t)N * TZC);
         cudaError_t e = set_smem(k_yexp2<N, TZC>, smem);
         if (e != cudaSuccess) return e;
-        k_yexp2<N, TZC><<<grid, TZC / 2 * PC, smem, s>>>(a, g.tw, (float)g.kF);
+        k_yexp2<N, TZC><<<grid, TZC / 2 * PC, smem, s>>>(a, g.tw, kDerivUnit);
         return cudaGetLastError();
     }
     template <bool PF = false>
@@ -1458,7 +1458,7 @@ struct Launch {
         const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PF ? 2 : 1));
         cudaError_t e = set_smem(k_yexp<N, TZC, PF>, smem);
         if (e != cudaSuccess) return e;
-        k_yexp<N, TZC, PF><<<grid, TZC * PC, smem, s>>>(a, g.tw, (float)g.kF);
+        k_yexp<N, TZC, PF><<<grid, TZC * PC, smem, s>>>(a, g.tw, kDerivUnit);
         return cudaGetLastError();
     }
     template <bool PF>
@@ -1468,7 +1468,7 @@ struct Launch {
         const size_t smem = sizeof(float2) * (N + (PF ? 3 : 2) * (size_t)TZZ * PITCH);
         cudaError_t e = set_smem(k_zexp<N, TZZ, PF>, smem);
         if (e != cudaSuccess) return e;
-        k_zexp<N, TZZ, PF><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+        k_zexp<N, TZZ, PF><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, kDerivUnit);
         return cudaGetLastError();
     }
     // TMA-staged y expansion: 8-column tiles, two tile buffers per block
@@ -1494,7 +1494,7 @@ struct Launch {
         const size_t smem = 2 * (size_t)N * TZ * sizeof(float2) + sizeof(float2) * N + 1024;   // + alignment slack
         if ((e = set_smem(k_yexp_tma<N, TZ>, smem)) != cudaSuccess) return e;
         dim3 grid(M / TZ, N);
-        k_yexp_tma<N, TZ><<<grid, TZ * PC, smem, s>>>(a, map, g.tw, (float)g.kF, g.status);
+        k_yexp_tma<N, TZ><<<grid, TZ * PC, smem, s>>>(a, map, g.tw, kDerivUnit, g.status);
         return cudaGetLastError();
     }
     static cudaError_t zexp_pairs(const Geo& g, const ZPairArgs& a, cudaStream_t s) {
@@ -1504,10 +1504,10 @@ struct Launch {
         cudaError_t e;
         if (a.ntargets <= 1) {
             if ((e = set_smem(k_zexp_pairs<N, TZZ, 1>, smem)) != cudaSuccess) return e;
-            k_zexp_pairs<N, TZZ, 1><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+            k_zexp_pairs<N, TZZ, 1><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, kDerivUnit);
         } else {
             if ((e = set_smem(k_zexp_pairs<N, TZZ, 2>, smem)) != cudaSuccess) return e;
-            k_zexp_pairs<N, TZZ, 2><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, (float)g.kF);
+            k_zexp_pairs<N, TZZ, 2><<<grid, TZZ * PZ, smem, s>>>(a, g.tw, kDerivUnit);
         }
         return cudaGetLastError();
     }
@@ -1535,7 +1535,7 @@ struct Launch {
             const long long need = (groups + kRowWarps - 1) / kRowWarps;
             const long long resident = (long long)(per > 0 ? per : 1) * sms;
             k_zrow<N, NT, BAND><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
-                a, g.tw, (float)g.kF);
+                a, g.tw, kDerivUnit);
             return cudaGetLastError();
         }
     }

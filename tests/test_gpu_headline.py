@@ -14,12 +14,13 @@
   0.01-0.4 h/Mpc, and the tree-level equilateral bispectrum B_tree = 3 E in 16
   shells over [0, K_c).
 
-P-term bar, per bin with N_k > 0 and |P| > 1e-3 max |P|: max(1e-5 |P|, 6
-sigma_b), sigma_b the standard deviation of the bin's error under white noise of
-the level s_n the GPU's delta_n carries (its RMS error per mode below the cut,
-measured here; tests/fp32_floor.py). 1e-5 holds wherever FP32 fields can hold
-it; in the low-k bins of the two-loop terms FP32 rounding of the real-space
-orders alone exceeds it (tests/test_fp32_floor.py). The noise level itself is
+P-term bar, per bin with N_k > 0 and |P| > 1e-3 max |P|: 1e-5 |P| for P11 and
+P22; max(1e-5 |P|, 6 sigma_b) for the loop terms P13, P33, P24, P15, sigma_b
+the standard deviation of the bin's error under white noise of the level s_n
+the GPU's delta_n carries (its RMS error per mode below the cut, measured
+here; tests/fp32_floor.py). 1e-5 holds wherever FP32 fields can hold it; in
+the low-k bins of the loop terms FP32 rounding of the real-space orders alone
+exceeds it (tests/test_fp32_floor.py). The noise level itself is
 bounded independently: s_n of the GPU must not exceed 1.5 times that of an
 independent FP32 implementation of the recursion (single-precision transforms
 and products on the CPU) on the same input.
@@ -171,10 +172,13 @@ def test_c2_pterms_match_oracle(c2):
             "bins_on_fp32_floor": int((used & sel).sum()), "max_rel": float(f"{rel.max():.2e}"),
             "median_rel": float(f"{np.median(rel):.2e}"),
             "max_err_over_sigma": float(f"{np.max(err[sel] / np.maximum(sig[sel], 1e-300)):.2f}")}
-        assert np.all(err[sel] <= bar[sel]), ((i, j), np.max(err[sel] / bar[sel]))
-        if (i, j) in ((1, 1), (1, 3), (2, 2)):
-            assert np.all(rel <= 1e-5), ((i, j), rel.max())
+        report["terms"][f"P{i}{j}"]["max_err_over_bar"] = float(f"{np.max(err[sel] / bar[sel]):.3f}")
     print("C2_PTERMS " + json.dumps(report))
+    for i, j in TERMS:
+        t = report["terms"][f"P{i}{j}"]
+        assert t["max_err_over_bar"] <= 1.0, ((i, j), t)
+        if j <= 2:
+            assert t["max_rel"] <= 1e-5, ((i, j), t)
 
 
 def test_c2_tree_bispectrum_matches_oracle(c2):
