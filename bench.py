@@ -116,37 +116,76 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- oracle arm
-def oracle_sample(target_s=12.0):
-    """FP64 oracle on a bounded sample of the workload: one realisation of a
-    64^3 grid with the same cell size (L = 250 Mpc/h), orders 1..5 (initial
-    field + recursion), repeated until about target_s seconds of CPU work."""
-    import numpy as np  # noqa: F401
+def cpu_model():
+    """The host CPU's model name (lscpu / /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(args):
+    """One worker of the oracle sample: realisations of an n^3 grid (same cell
+    size as the workload) for about target_s seconds; returns their count."""
+    n, target_s, seed0 = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import cosmology, spt
-    n, L = 64, BOX * 64 / N_GRID
+    L = BOX * n / N_GRID
     A = cosmology.amplitude(cosmology.DEFAULT_COSMO)
     reps, t0 = 0, time.perf_counter()
     while True:
-        d1 = spt.linear_field(n, L, N_MAX, cosmology.DEFAULT_COSMO, 1000 + reps, A=A)
+        d1 = spt.linear_field(n, L, N_MAX, cosmology.DEFAULT_COSMO, seed0 + reps, A=A)
         spt.run_orders(d1, L, N_MAX)
         reps += 1
-        el = time.perf_counter() - t0
-        if el >= target_s:
-            break
+        if time.perf_counter() - t0 >= target_s:
+            return reps
+
+
+def oracle_sample(target_s=12.0, n=64, workers=1):
+    """FP64 oracle on a bounded sample of the workload: realisations of an n^3
+    grid with the same cell size (L = 2000 n / 512 Mpc/h), orders 1..5 (initial
+    field + recursion), for about target_s seconds, on `workers` host cores (one
+    process each, started with spawn; numpy's transforms are single threaded).
+    Returns (Mcells*orders/s, seconds, realisations, cpu_baseline record)."""
+    t0 = time.perf_counter()
+    if workers <= 1:
+        reps = _oracle_worker((n, target_s, 1000))
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            reps = sum(pool.map(_oracle_worker, [(n, target_s, 1000 + 100000 * w) for w in range(workers)]))
+    el = time.perf_counter() - t0
     value = reps * n ** 3 * N_MAX / el / 1e6
-    return value, el, reps, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{reps} realisation(s) of 64^3, L=250 Mpc/h (same cell size), n_max=5, "
-                                       f"IC + recursion, numpy FP64 single thread, {el:.1f} s"}
+    L = BOX * n / N_GRID
+    return value, el, reps, {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                             "sample": f"{reps} realisation(s) of {n}^3, L={L:g} Mpc/h (same cell size), n_max=5, "
+                                       f"IC + recursion, numpy FP64, {workers} process(es), {el:.1f} s"}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on all host cores, a bounded sample
+    of the workload per step."""
     if rank != 0:
         return
+    workers = os.cpu_count() or 1
     vals = []
     for _ in range(args.warmup):
         oracle_sample(target_s=0.0)
     t_all = time.perf_counter()
+    cb = None
     for _ in range(args.steps):
-        v, el, reps, cb = oracle_sample(target_s=max(1.0, 30.0 / max(args.steps, 1)))
+        v, el, reps, cb = oracle_sample(target_s=max(1.0, 30.0 / max(args.steps, 1)), workers=workers)
         vals.append(v)
     total = time.perf_counter() - t_all
     value = statistics.median(vals)
@@ -159,6 +198,19 @@ def run_reference(args, rank, world):
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_cpu_sweep(args):
+    """The oracle at 64^3, 128^3 and 256^3 (same cell size as the workload) on
+    one core and on every core: Mcells*orders/s per size (one JSON line)."""
+    out = {"cpu_model": cpu_model(), "nproc": os.cpu_count(), "sizes": {}}
+    for n, t in ((64, 20.0), (128, 30.0), (256, 60.0)):
+        one = oracle_sample(target_s=t, n=n, workers=1)
+        allc = oracle_sample(target_s=t, n=n, workers=os.cpu_count() or 1)
+        out["sizes"][f"{n}^3"] = {"one_core": round(one[0], 3), "all_cores": round(allc[0], 3),
+                                  "one_core_s_per_realisation": round(one[1] / one[2], 2),
+                                  "all_cores_realisations": allc[2]}
+    print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------------------- GPU arm
@@ -310,6 +362,27 @@ def run_gpu(args, rank, world):
     t0 = time.perf_counter()
     e2e_run(args.steps)
     e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, dist, "cuda")
+
+    # end to end from the library's own host input, the seeds (a host array the
+    # initial-field call takes), to the binned statistics read back to the host
+    def e2e_seeds_run(nsteps):
+        for st in range(nsteps):
+            k = st % 2
+            g.make_linear_field(plan, seeds, out=d1)
+            orders_and_estimators(d1)
+            host_out[k][: B * 192].copy_(pout.view(-1), non_blocking=True)
+            host_out[k][B * 192:].copy_(bout.view(-1), non_blocking=True)
+            d2h_done[k].record(stream)
+            if st >= 1:
+                d2h_done[1 - k].synchronize()
+        d2h_done[(nsteps - 1) % 2].synchronize()
+
+    e2e_seeds_run(2)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_seeds_run(args.steps)
+    e2e_seeds_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, dist, "cuda")
     del d1b[1]
     # the host -> device link rate of the same copy alone (it varies between
     # machines and dominates the difference between e2e and the device timing)
@@ -352,7 +425,9 @@ def run_gpu(args, rank, world):
     breakdown = {k: {"launches": v[0], "ms_per_step": round(v[1] / args.steps, 3),
                      "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
-    cpu_value, el, reps, cb = oracle_sample()
+    cpu_value, el, reps, cb = oracle_sample(target_s=10.0, workers=os.cpu_count() or 1)
+    one = oracle_sample(target_s=6.0, workers=1)
+    cb["one_core"] = {"value": one[0], "sample": one[3]["sample"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -378,6 +453,10 @@ def run_gpu(args, rank, world):
                 "path": "delta_1(k) from pinned host -> run_orders -> estimators -> host; each step's copy "
                         "in overlaps the previous step's compute (two device buffers, copy stream); each "
                         "step's read-back is awaited once the next step is queued (two pinned buffers)"},
+        "e2e_seeds": {"value": work / (e2e_seeds_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * B,
+                      "d2h_bytes_per_step": int(host_out[0].numel() * 8), "ms_per_step": e2e_seeds_ms,
+                      "path": "seeds (host array, the initial-field call's input) -> make_linear_field -> "
+                              "run_orders -> estimators -> statistics read back to pinned host memory"},
         "cpu_baseline": cb,
         "autotune": tuning,
         "recursion_graph": {"ms_per_launch": round(graph_ms, 3), "realisations": B,
@@ -488,9 +567,45 @@ def mixed_batch(args):
     same = all(torch.equal(a, b) for a, b in zip(batch.spectra, eager_sp))
     cells = sum(4 * n ** 3 for n, _ in sizes)
     batch.close()
+    # the same twelve realisations as ONE launch of the persistent work-queue
+    # kernel; and with one plan (own workspace) per realisation, so that all
+    # twelve chains can run concurrently
+    def queue_ms(multi):
+        for _ in range(3):
+            multi.launch()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            multi.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    multi = g.Multi(plans, d1s, wss=eager_ws)
+    q_ms = queue_ms(multi)
+    q_same = all(torch.equal(a, b) for a, b in zip(multi.spectra, eager_sp))
+    multi.close()
+    del eager_ws
+    torch.cuda.empty_cache()
+    singles, sd1 = [], []
+    for i, (n, L) in enumerate(sizes):
+        for j in range(4):
+            p1 = g.Plan(n, N_MAX, L)
+            g.set_tuning(p1, g.get_tuning(plans[i]))
+            singles.append(p1)
+            sd1.append(d1s[i][j:j + 1].contiguous())
+    multi12 = g.Multi(singles, sd1)
+    q12_ms = queue_ms(multi12)
+    q12_same = all(torch.equal(multi12.spectra[4 * i + j], eager_sp[i][j:j + 1])
+                   for i in range(3) for j in range(4))
+    multi12.close()
     return {"grids": "128^3, 192^3, 256^3 x 4 seeds, n_max=5", "graph_ms": round(graph_ms, 3),
             "eager_ms": round(eager_ms, 3), "value": round(cells * N_MAX / graph_ms / 1e3, 1), "unit": UNIT,
-            "bitwise_equal_to_eager": bool(same)}
+            "bitwise_equal_to_eager": bool(same),
+            "persistent_queue": {"ms": round(q_ms, 3), "value": round(cells * N_MAX / q_ms / 1e3, 1),
+                                 "launches": 1, "chains": 3, "bitwise_equal_to_eager": bool(q_same)},
+            "persistent_queue_12_chains": {"ms": round(q12_ms, 3), "value": round(cells * N_MAX / q12_ms / 1e3, 1),
+                                           "launches": 1, "chains": 12,
+                                           "bitwise_equal_to_eager": bool(q12_same)}}
 
 
 def cufft_comparator(N, L, tuning):
@@ -649,6 +764,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--quick", action="store_true", help="skip the mixed-batch and emulator sections")
     ap.add_argument("--emu-steps", type=int, default=20000)
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="time the FP64 oracle at 64^3, 128^3, 256^3 on one and on all host cores")
     ap.add_argument("--case", choices=["c2r", "r2c", "orders", "power", "bispec"],
                     help="run one small library case for a profiler instead of the benchmark")
     ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
@@ -658,6 +775,9 @@ def main():
     args = ap.parse_args()
     if args.case:
         run_case(args)
+        return
+    if args.cpu_sweep:
+        run_cpu_sweep(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -1102,6 +1102,26 @@ gridspt_status gridspt_multi_create(const gridspt_plan* plans, int32_t count, co
         t_queue = nullptr;
         if (st != GRIDSPT_OK) return st;
     }
+    // z passes of N = 3 * 2^a with two pair targets become two stages of one
+    // target each (the z expansion is repeated; each target's sums are those
+    // of the two-target pass, term by term)
+    for (auto& ch : chains) {
+        std::vector<QStage> out;
+        for (const QStage& st : ch) {
+            if (st.kind == Q_Z && st.z.ntargets == 2 && st.N % 3 == 0) {
+                QStage a = st, b = st;
+                a.z.ntargets = 1;
+                b.z.ntargets = 1;
+                b.z.t[0] = st.z.t[1];
+                b.z.store = nullptr;
+                out.push_back(a);
+                out.push_back(b);
+            } else {
+                out.push_back(st);
+            }
+        }
+        ch.swap(out);
+    }
     // interleave the chains by cumulative work: the next stage comes from the
     // chain that has been given the least work so far
     std::vector<QStage> q;
@@ -1120,10 +1140,19 @@ gridspt_status gridspt_multi_create(const gridspt_plan* plans, int32_t count, co
         q.push_back(s);
     }
     const int nst = (int)q.size();
+    // tiles per ticket: about four tickets per resident block in a stage's
+    // share of the GPU, at most 8 tiles (fewer atomics and waits per tile,
+    // small enough that a stage's last tickets do not leave the GPU idle)
+    int sms = 1;
+    if (gridspt_status st = set_device(plans[0])) return st;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plans[0]->device), "SM count");
+    const long long blocks = 2LL * sms;
     std::vector<long long> starts(nst + 1, 0);
     for (int i = 0; i < nst; ++i) {
+        q[i].chunk = std::max<long long>(1, std::min<long long>(8, q[i].ntiles / (8 * blocks)));
+        q[i].nticks = (q[i].ntiles + q[i].chunk - 1) / q[i].chunk;
         q[i].tile0 = starts[i];
-        starts[i + 1] = starts[i] + q[i].ntiles;
+        starts[i + 1] = starts[i] + q[i].nticks;
     }
     if (fault_inject("queue_stall") && nst > 1) q[nst / 2].nosignal = 1;
     gridspt_multi m = new (std::nothrow) gridspt_multi_s();

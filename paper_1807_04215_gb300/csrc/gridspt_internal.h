@@ -298,6 +298,8 @@ struct QStage {
     int dep;               // stage this one waits for (-1: none)
     int nosignal;          // fault injection: this stage never counts its tiles done
     long long ntiles;
+    long long chunk;       // tiles per ticket (set by the host: larger stages take several per ticket)
+    long long nticks;      // tickets of the stage, ceil(ntiles / chunk)
     long long tile0;       // first ticket of the stage
     int gx, gy;            // virtual grid of the column passes (tile = bx + gx (by + gy bz))
     int count;             // fields of Q_ZR2C / Q_COLY / Q_COLX
@@ -319,10 +321,11 @@ struct QStage {
 // Supported grid sizes of the queue kernel (its tile bodies are instantiated
 // for these); false for the others.
 bool queue_supported_n(int N);
-// Tiles of a stage whose kind, N and arguments are set (fills gx, gy, ntiles).
+// Tiles of a stage whose kind, N and arguments are set (fills gx, gy, ntiles;
+// chunk = 1).
 void queue_tiles(QStage& st);
 // Launch over `nst` stages already in device memory (stages, starts[nst + 1]
-// first tickets with starts[nst] = total), with hdr (2 + nst ints, zeroed by
+// first tickets with starts[nst] = total), with hdr (4 + nst ints, zeroed by
 // this call on `s`): ticket counter, abort flag, per-stage done counters.
 cudaError_t launch_queue(const QStage* stages, const long long* starts, int nst, long long total, int* hdr,
                          int* status, long long wait_ns, cudaStream_t s);

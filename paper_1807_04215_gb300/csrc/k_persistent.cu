@@ -27,10 +27,11 @@
 //
 // Tile bodies: the column passes (x expansion, y expansion, forward column
 // passes) run the bodies of k_transform.cuh with tile widths that give 256
-// threads; the z passes run on warp rows (P = M / E lanes per row) as in
-// k_zrow, but read partner fields straight from global memory instead of
-// staging them in shared memory, so that a block of every supported size
-// fits twice per SM; the diagonal pairs run product_cells. Accumulation
+// threads; the z passes run the warp-row body of k_zrow (one row group per
+// warp) for power-of-two N, and for N = 3 * 2^a a warp-row form that reads the
+// partner fields straight from global memory instead of staging them in
+// shared memory (their staged rows would not fit twice per SM); the diagonal
+// pairs run product_cells. Accumulation
 // orders and transform arithmetic are those of the separate kernels, so the
 // results are bitwise equal to gridspt_run_orders.
 #include "k_transform.cuh"
@@ -78,7 +79,7 @@ __device__ __forceinline__ void q_tables(float2* twl, float2* twp, const float2*
 // one group of RW rows per warp, 8 groups per tile.
 template <int N, int NT, bool BAND>
 __device__ void q_zrow(const ZPairArgs& args, const float2* __restrict__ twg, float kF, long long tile,
-                       float2* sm) {
+                       float2* sm, bool table_ready) {
     using C = QRow<N>;
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW, WIN = C::WIN;
     constexpr int NA = NT > 0 ? NT : 1;
@@ -86,7 +87,7 @@ __device__ void q_zrow(const ZPairArgs& args, const float2* __restrict__ twg, fl
     float2* twp = twl + C::NTW * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane / P, p = lane - r * P;
-    q_tables<N>(twl, twp, twg);
+    if (!table_ready) q_tables<N>(twl, twp, twg);
     float2* wbase = sm + C::HDR + warp * C::WSTRIDE;
     float2* xrow = wbase + WIN + r * C::XROW;
     const YZExpArgs& z = args.z;
@@ -206,14 +207,14 @@ __device__ void q_zrow(const ZPairArgs& args, const float2* __restrict__ twg, fl
 
 // Contiguous-axis forward transform of k_zrow_r2c, one row group per warp.
 template <int N>
-__device__ void q_zr2c(const QStage& st, long long tile, float2* sm) {
+__device__ void q_zr2c(const QStage& st, long long tile, float2* sm, bool table_ready) {
     using C = QRow<N>;
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW;
     float2* twl = sm;
     float2* twp = twl + C::NTW * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane / P, p = lane - r * P;
-    q_tables<N>(twl, twp, st.tw);
+    if (!table_ready) q_tables<N>(twl, twp, st.tw);
     float2* xrow = sm + C::HDR + warp * C::WSTRIDE + C::WIN + r * C::XROW;
     const long long per = (long long)N * N / RW;
     const long long grp = tile * (kQueueThreads / 32) + warp;
@@ -240,31 +241,54 @@ __device__ void q_zr2c(const QStage& st, long long tile, float2* sm) {
     }
 }
 
+// Layout class of the table a stage kind keeps at the start of shared memory:
+// 1 the column table of the transforms, 2 the warp-row tables of k_zrow, 3 the
+// warp-row tables of QRow (0: none).
+__host__ __device__ constexpr int q_table_class(int kind, bool row_ok) {
+    return (kind == Q_XEXP0 || kind == Q_XEXP1 || kind == Q_YEXP || kind == Q_COLY || kind == Q_COLX) ? 1
+           : kind == Q_Z ? (row_ok ? 2 : 3) : kind == Q_ZR2C ? 3 : 0;
+}
+
 template <int N>
-__device__ void q_tile(const QStage& st, long long tile, float2* sm) {
+__device__ void q_tile(const QStage& st, long long tile, float2* sm, bool tr) {
     constexpr int TZ = qtz<N>();
     const int bx = (int)(tile % st.gx);
     const long long rest = tile / st.gx;
     const int by = (int)(rest % st.gy);
     const int bz = (int)(rest / st.gy);
     switch (st.kind) {
-        case Q_XEXP0: xexp_body<N, TZ, 0>(st.x, st.tw, st.kF, st.inv_kF2, bx, by, sm); break;
-        case Q_XEXP1: xexp_body<N, TZ, 1>(st.x, st.tw, st.kF, st.inv_kF2, bx, by, sm); break;
-        case Q_YEXP: yexp_body<N, TZ, false>(st.y, st.tw, st.kF, bx, by, sm); break;
-        case Q_COLY: colpass_body<N, TZ, 1, false>(st.data, st.fstride, st.tw, -1, 0, bx, by, bz, sm); break;
-        case Q_COLX: colpass_body<N, TZ, 0, true>(st.data, st.fstride, st.tw, st.s2, st.zero_k0, bx, by, bz, sm); break;
-        case Q_ZR2C: q_zr2c<N>(st, tile, sm); break;
+        case Q_XEXP0: xexp_body<N, TZ, 0>(st.x, st.tw, st.kF, st.inv_kF2, bx, by, sm, tr); break;
+        case Q_XEXP1: xexp_body<N, TZ, 1>(st.x, st.tw, st.kF, st.inv_kF2, bx, by, sm, tr); break;
+        case Q_YEXP: yexp_body<N, TZ, false>(st.y, st.tw, st.kF, bx, by, sm, tr); break;
+        case Q_COLY: colpass_body<N, TZ, 1, false>(st.data, st.fstride, st.tw, -1, 0, bx, by, bz, sm, tr); break;
+        case Q_COLX: colpass_body<N, TZ, 0, true>(st.data, st.fstride, st.tw, st.s2, st.zero_k0, bx, by, bz, sm, tr);
+            break;
+        case Q_ZR2C: q_zr2c<N>(st, tile, sm, tr); break;
         case Q_Z: {
             const bool band = st.z.z.band > 0;
+            if constexpr (RowCfg<N>::ok) {   // power-of-two rows: the z pass of k_zrow (staged partners, prefetch)
+                constexpr long long one = 1LL << 40;   // a stride past every group: one group per warp
+                const long long g0 = tile * (kQueueThreads / 32);
+                if (st.z.ntargets == 0) {
+                    if (band) zrow_body<N, 0, true>(st.z, st.tw, st.kF, g0, one, sm, tr);
+                    else zrow_body<N, 0, false>(st.z, st.tw, st.kF, g0, one, sm, tr);
+                } else if (st.z.ntargets == 1) {
+                    if (band) zrow_body<N, 1, true>(st.z, st.tw, st.kF, g0, one, sm, tr);
+                    else zrow_body<N, 1, false>(st.z, st.tw, st.kF, g0, one, sm, tr);
+                } else {
+                    if (band) zrow_body<N, 2, true>(st.z, st.tw, st.kF, g0, one, sm, tr);
+                    else zrow_body<N, 2, false>(st.z, st.tw, st.kF, g0, one, sm, tr);
+                }
+                break;
+            }
+            // N = 3 * 2^a: one target per stage (the host splits two-target
+            // launches), which keeps the accumulators of 12-element rows in registers
             if (st.z.ntargets == 0) {
-                if (band) q_zrow<N, 0, true>(st.z, st.tw, st.kF, tile, sm);
-                else q_zrow<N, 0, false>(st.z, st.tw, st.kF, tile, sm);
-            } else if (st.z.ntargets == 1) {
-                if (band) q_zrow<N, 1, true>(st.z, st.tw, st.kF, tile, sm);
-                else q_zrow<N, 1, false>(st.z, st.tw, st.kF, tile, sm);
+                if (band) q_zrow<N, 0, true>(st.z, st.tw, st.kF, tile, sm, tr);
+                else q_zrow<N, 0, false>(st.z, st.tw, st.kF, tile, sm, tr);
             } else {
-                if (band) q_zrow<N, 2, true>(st.z, st.tw, st.kF, tile, sm);
-                else q_zrow<N, 2, false>(st.z, st.tw, st.kF, tile, sm);
+                if (band) q_zrow<N, 1, true>(st.z, st.tw, st.kF, tile, sm, tr);
+                else q_zrow<N, 1, false>(st.z, st.tw, st.kF, tile, sm, tr);
             }
             break;
         }
@@ -283,31 +307,46 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// hdr: [0..1] ticket counter (64-bit), [2] abort flag, [3] unused, [4 + s] done tiles of stage s
+// hdr: [0..1] ticket counter (64-bit), [2] abort flag, [3] unused, [4 + s] done tickets of stage s.
+// A ticket covers `chunk` consecutive tiles of its stage. Thread 0 takes the
+// block's next ticket while the current one runs (the atomic's latency is
+// hidden); a block that has seen a stage complete remembers it (a bit per
+// stage in shared memory) and does not read its counter again.
+constexpr int kQueueBitStages = 8192;
+
 __global__ void __launch_bounds__(kQueueThreads, 2)
 k_queue(const QStage* __restrict__ stages, const long long* __restrict__ starts, int nst, long long total,
         int* __restrict__ hdr, int* __restrict__ status, long long wait_ns) {
     extern __shared__ __align__(16) float2 sm[];
     __shared__ long long s_ticket;
     __shared__ int s_stage, s_abort;
+    __shared__ unsigned s_seen[kQueueBitStages / 32];   // stages this block has seen complete
+    __shared__ int s_tabkey;                            // layout class and N of the table in sm (0: none)
     unsigned long long* next = reinterpret_cast<unsigned long long*>(hdr);
     int* abort_flag = hdr + 2;
     int* done = hdr + 4;
+    for (int i = threadIdx.x; i < kQueueBitStages / 32; i += blockDim.x) s_seen[i] = 0u;
+    if (threadIdx.x == 0) s_tabkey = 0;
+    __syncthreads();
+    long long t_next = 0;
+    if (threadIdx.x == 0) t_next = (long long)atomicAdd(next, 1ull);
     for (;;) {
         if (threadIdx.x == 0) {
-            long long t = (long long)atomicAdd(next, 1ull);
+            const long long t = t_next;
             int ab = *reinterpret_cast<volatile int*>(abort_flag);
             int s = -1;
             if (t < total && !ab) {
-                int lo = 0, hi = nst;                     // starts[lo] <= t < starts[hi]
+                t_next = (long long)atomicAdd(next, 1ull);    // used at the next iteration
+                int lo = 0, hi = nst;                          // starts[lo] <= t < starts[hi]
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
-                    if (starts[mid] <= t) lo = mid; else hi = mid;
+                    if (__ldg(starts + mid) <= t) lo = mid; else hi = mid;
                 }
                 s = lo;
-                const int dep = stages[s].dep;
-                if (dep >= 0) {                           // bounded wait for the predecessor stage
-                    const int need = (int)stages[dep].ntiles;
+                const int dep = __ldg(&stages[s].dep);
+                const bool known = dep < kQueueBitStages && dep >= 0 && ((s_seen[dep >> 5] >> (dep & 31)) & 1u);
+                if (dep >= 0 && !known) {                      // bounded wait for the predecessor stage
+                    const int need = (int)(__ldg(starts + dep + 1) - __ldg(starts + dep));
                     const unsigned long long t0 = global_ns();
                     while (ld_acquire(done + dep) < need) {
                         if (*reinterpret_cast<volatile int*>(abort_flag)) { ab = 1; break; }
@@ -317,8 +356,9 @@ k_queue(const QStage* __restrict__ stages, const long long* __restrict__ starts,
                             ab = 1;
                             break;
                         }
-                        __nanosleep(200);
+                        __nanosleep(100);
                     }
+                    if (!ab && dep < kQueueBitStages) s_seen[dep >> 5] |= 1u << (dep & 31);
                 }
             }
             s_ticket = t;
@@ -329,36 +369,44 @@ k_queue(const QStage* __restrict__ stages, const long long* __restrict__ starts,
         if (s_abort) return;
         const int s = s_stage;
         const QStage& st = stages[s];
-        const long long tile = s_ticket - starts[s];
-        if (st.kind == Q_PRODUCT) {
-            const long long i = tile * kQueueThreads + threadIdx.x;
-            if (i < st.pr.cells / 4) product_cells(st.pr, i, PlainLoad{});
-        } else if (st.kind == Q_ZEROBAND) {
-            const int Nn = st.N, H = Nn / 4, band = st.band;
-            const long long pairs = (long long)Nn * Nn * H;
-            const long long j = tile * kQueueThreads + threadIdx.x;
-            if (j < 2 * pairs) {
-                const int fld = (int)(j / pairs);
-                const long long i2 = j - fld * pairs;
-                const long long row = i2 / H;
-                const int kz = (int)(2 * (i2 - row * H));
-                const int ky = (int)(row % Nn);
-                if (!(kz < band && (ky < band || ky > Nn - band)))
-                    reinterpret_cast<float4*>(fld ? st.data2 : st.data)[i2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const long long first = (s_ticket - starts[s]) * st.chunk;
+        const long long last = first + st.chunk < st.ntiles ? first + st.chunk : st.ntiles;
+        for (long long tile = first; tile < last; ++tile) {
+            if (st.kind == Q_PRODUCT) {
+                const long long i = tile * kQueueThreads + threadIdx.x;
+                if (i < st.pr.cells / 4) product_cells(st.pr, i, PlainLoad{});
+            } else if (st.kind == Q_ZEROBAND) {
+                const int Nn = st.N, H = Nn / 4, band = st.band;
+                const long long pairs = (long long)Nn * Nn * H;
+                const long long j = tile * kQueueThreads + threadIdx.x;
+                if (j < 2 * pairs) {
+                    const int fld = (int)(j / pairs);
+                    const long long i2 = j - fld * pairs;
+                    const long long row = i2 / H;
+                    const int kz = (int)(2 * (i2 - row * H));
+                    const int ky = (int)(row % Nn);
+                    if (!(kz < band && (ky < band || ky > Nn - band)))
+                        reinterpret_cast<float4*>(fld ? st.data2 : st.data)[i2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else {
+                const int cls = q_table_class(st.kind, (st.N & (st.N - 1)) == 0);
+                const int key = cls ? (cls << 16) | st.N : 0;
+                const bool tr = key != 0 && s_tabkey == key;
+                switch (st.N) {
+                    case 64: q_tile<64>(st, tile, sm, tr); break;
+                    case 96: q_tile<96>(st, tile, sm, tr); break;
+                    case 128: q_tile<128>(st, tile, sm, tr); break;
+                    case 192: q_tile<192>(st, tile, sm, tr); break;
+                    case 256: q_tile<256>(st, tile, sm, tr); break;
+                    default: break;
+                }
+                __syncthreads();                          // every thread has read s_tabkey
+                if (threadIdx.x == 0) s_tabkey = key;
             }
-        } else {
-            switch (st.N) {
-                case 64: q_tile<64>(st, tile, sm); break;
-                case 96: q_tile<96>(st, tile, sm); break;
-                case 128: q_tile<128>(st, tile, sm); break;
-                case 192: q_tile<192>(st, tile, sm); break;
-                case 256: q_tile<256>(st, tile, sm); break;
-                default: break;
-            }
+            __syncthreads();                              // shared buffers free, every store issued
         }
-        __syncthreads();                                  // every thread's stores are issued
         if (threadIdx.x == 0) {
-            __threadfence();                              // ... and visible before the count
+            __threadfence();                              // the ticket's stores are visible before the count
             if (!st.nosignal) atomicAdd(done + s, 1);
         }
     }
@@ -366,7 +414,8 @@ k_queue(const QStage* __restrict__ stages, const long long* __restrict__ starts,
 
 template <int N>
 constexpr size_t q_smem_n() {
-    return QRow<N>::smem > col_smem<N>() ? QRow<N>::smem : col_smem<N>();
+    constexpr size_t z = RowCfg<N>::ok ? RowCfg<N>::smem(2) : QRow<N>::smem;
+    return z > col_smem<N>() ? z : col_smem<N>();
 }
 
 }  // namespace
@@ -430,6 +479,7 @@ void tiles_n(QStage& st) {
 }  // namespace
 
 void queue_tiles(QStage& st) {
+    st.chunk = 1;
     switch (st.N) {
         case 64: tiles_n<64>(st); break;
         case 96: tiles_n<96>(st); break;

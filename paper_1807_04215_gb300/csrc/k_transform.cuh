@@ -136,16 +136,19 @@ __device__ __forceinline__ void tile_store(float2* dst, const float2* tile, long
 // The pass bodies below take their block coordinates (bx, by, bz) and shared
 // memory explicitly, so that the same code runs as a kernel of its own (block
 // coordinates from blockIdx) and as a tile of the persistent work-queue kernel
-// (k_persistent.cu); the block has TZ * P threads either way.
+// (k_persistent.cu); the block has TZ * P threads either way. table_ready:
+// the twiddle table already sits at the start of sm (a previous tile of the
+// same size and table layout in the same block loaded it, and every thread
+// has passed a block barrier since).
 template <int N, int TZ, int AXIS, bool FIN>
 __device__ __forceinline__ void colpass_body(float2* __restrict__ data, long long fstride,
                                              const float2* __restrict__ twg, long long s2_nl, int zero_k0,
-                                             int bx, int by, int bz, float2* sm) {
+                                             int bx, int by, int bz, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
     float2* tw = sm;
     float2* buf = sm + N;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    load_table(tw, twg, N);
+    if (!table_ready) load_table(tw, twg, N);
     const int kz = bx * TZ + c;
     const int a = by;
     const bool act = kz < M;
@@ -248,12 +251,12 @@ __host__ __device__ constexpr int xexp_min_blocks() {
 // (written to src0, src1 and finalised like MODE 1).
 template <int N, int TZ, int MODE>
 __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __restrict__ twg, float kF,
-                                          float inv_kF2, int bx, int by, float2* sm) {
+                                          float inv_kF2, int bx, int by, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
     float2* tw = sm;
     float2* buf = sm + N;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    load_table(tw, twg, N);
+    if (!table_ready) load_table(tw, twg, N);
     const int kz = bx * TZ + c;
     const int B = args.band;
     const int ky = (B > 0 && by >= B) ? N - (2 * B - 1 - by) : by;   // band rows: [0, B) and (N - B, N)
@@ -385,13 +388,13 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
 // of the current input are transformed.
 template <int N, int TZ, bool PF>
 __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* __restrict__ twg, float kF, int bx,
-                                          int by, float2* sm) {
+                                          int by, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
     float2* tw = sm;
     float2* buf = sm + N;
     float2* pre = buf + N * TZ;                  // PF: next input tile, element (n, c) at n * TZ + c
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    load_table(tw, twg, N);
+    if (!table_ready) load_table(tw, twg, N);
     const int kz = bx * TZ + c;
     const int xr = by;
     const int B = args.band;
@@ -808,19 +811,24 @@ __device__ __forceinline__ void zrow_tables(float2* twl, float2* twp, const floa
     __syncthreads();
 }
 
+// Body of the warp-row z pass: warp w of the block handles the row groups
+// grp0 + w, grp0 + w + gstride, ... (the kernel: grp0 = blockIdx.x * kRowWarps,
+// gstride = gridDim.x * kRowWarps; a tile of the persistent queue: one group
+// per warp). Inputs, partners and partial sums are read through L2 (cp.async.cg
+// and ordinary loads), never through the read-only data path, so the body is
+// also correct for fields written earlier in the same launch.
 template <int N, int NT, bool BAND>
-__global__ void __launch_bounds__(kRowWarps * 32, NT == 0 ? 3 : 2)
-k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
+__device__ __forceinline__ void zrow_body(const ZPairArgs& args, const float2* __restrict__ twg, float kF,
+                                          long long grp0, long long gstride, float2* sm, bool table_ready = false) {
     using C = RowCfg<N>;
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW, WIN = C::WIN;
     constexpr int NA = NT > 0 ? NT : 1;
     static_assert(C::ok, "warp-row z pass needs P <= 32, 32 % P == 0 and a power-of-two row");
-    extern __shared__ __align__(16) float2 sm[];
     float2* twl = sm;                                  // [NTW][P] stage twiddles
     float2* twp = twl + C::NTW * P;                    // [E][P] pack twiddles tw[p + P i]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane / P, p = lane - r * P;
-    zrow_tables<N>(twl, twp, twg);
+    if (!table_ready) zrow_tables<N>(twl, twp, twg);
     float2* wbase = sm + C::HDR + warp * C::wstride(NT);
     float2* wpt = wbase + 2 * WIN;                                                 // [MAXP][RW][M] partners
     float2* xrow = wbase + WIN * (NT ? 2 + C::MAXP : 2) + r * C::XROW;              // this row's exchange buffer
@@ -836,11 +844,10 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
         if (B <= 0 || (2 * (lane + 32 * u)) % M < B) inb |= 1u << u;
     const long long rows = (long long)N * N;
     const long long groups = rows / RW;
-    const long long gstride = (long long)gridDim.x * kRowWarps;
     const long long fstride2 = args.cells / 2;
     int buf = 0;                 // wbase + buf * WIN holds the current input rows
     bool have_next = false;      // the other buffer holds (or receives) the next input
-    for (long long grp = (long long)blockIdx.x * kRowWarps + warp; grp < groups; grp += gstride) {
+    for (long long grp = grp0 + warp; grp < groups; grp += gstride) {
         const long long row0 = grp * RW, row = row0 + r;
         float2 accA[NA][E], accB[NA][E];
 #pragma unroll
@@ -875,7 +882,7 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                     float4 v[WIN / 64];
 #pragma unroll
                     for (int u = 0; u < WIN / 64; ++u)
-                        v[u] = ((inb >> u) & 1u) ? __ldg(src + lane + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[u] = ((inb >> u) & 1u) ? src[lane + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < WIN / 64; ++u) reinterpret_cast<float4*>(wbase + buf * WIN)[lane + 32 * u] = v[u];
                     __syncwarp();
@@ -962,7 +969,7 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
                     const float2* ib = reinterpret_cast<const float2*>(T.acc_in_b) + row * M;
 #pragma unroll
                     for (int i = 0; i < E; ++i) {
-                        const float2 va = __ldg(ia + p + P * i), vb = __ldg(ib + p + P * i);
+                        const float2 va = ia[p + P * i], vb = ib[p + P * i];
                         accA[t][i].x += va.x;
                         accA[t][i].y += va.y;
                         accB[t][i].x += vb.x;
@@ -981,6 +988,13 @@ k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
             }
         }
     }
+}
+
+template <int N, int NT, bool BAND>
+__global__ void __launch_bounds__(kRowWarps * 32, NT == 0 ? 3 : 2)
+k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
+    extern __shared__ __align__(16) float2 sm[];
+    zrow_body<N, NT, BAND>(args, twg, kF, (long long)blockIdx.x * kRowWarps, (long long)gridDim.x * kRowWarps, sm);
 }
 
 // ------------------------------------------------- TMA-staged y expansion
