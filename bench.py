@@ -200,14 +200,34 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def host_mem_bytes():
+    """Available host memory (MemAvailable), or None."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
 def run_cpu_sweep(args):
     """The oracle at 64^3, 128^3 and 256^3 (same cell size as the workload) on
-    one core and on every core: Mcells*orders/s per size (one JSON line)."""
+    one core and on every core: Mcells*orders/s per size (one JSON line). One
+    realisation of the FP64 oracle holds about 2 GB per 2 M cells (its derived
+    fields on full complex grids); the all-core run starts no more processes
+    than half the available host memory holds."""
     out = {"cpu_model": cpu_model(), "nproc": os.cpu_count(), "sizes": {}}
-    for n, t in ((64, 20.0), (128, 30.0), (256, 60.0)):
+    avail = host_mem_bytes()
+    for n, t in ((64, 10.0), (128, 20.0), (256, 1.0)):
+        per = 2.0e9 * n ** 3 / 2 ** 21
+        workers = os.cpu_count() or 1
+        if avail:
+            workers = max(1, min(workers, int(0.5 * avail / per)))
         one = oracle_sample(target_s=t, n=n, workers=1)
-        allc = oracle_sample(target_s=t, n=n, workers=os.cpu_count() or 1)
+        allc = oracle_sample(target_s=t, n=n, workers=workers)
         out["sizes"][f"{n}^3"] = {"one_core": round(one[0], 3), "all_cores": round(allc[0], 3),
+                                  "processes": workers,
                                   "one_core_s_per_realisation": round(one[1] / one[2], 2),
                                   "all_cores_realisations": allc[2]}
     print(json.dumps(out), flush=True)
