@@ -350,10 +350,13 @@ gridspt_status gridspt_multi_destroy(gridspt_multi multi);
 /* Autotuner for the transform passes (not part of the paper's method). Each
  * pass (0 forward column pass, 1 x expansion, 2 y expansion, 3 z expansion,
  * 4 contiguous-axis forward pass) has two variants for N >= 128 (identical for
- * smaller N). The y expansion has a third, TMA-staged one (N >= 128), a
- * fourth with two adjacent columns per thread (16-byte accesses) and a fifth
- * that copies the next input's columns by cp.async during the current
- * input's transforms. The z
+ * smaller N). The x expansion has two more (2, 3) that transform two outputs
+ * (and the two forward inputs) at a time in a shared exchange. The y
+ * expansion has a third, TMA-staged one (N >= 128), a fourth with two
+ * adjacent columns per thread (16-byte accesses), a fifth that copies the
+ * next input's columns by cp.async during the current input's transforms, and
+ * a sixth and seventh (5, 6) that transform two outputs of one input at a
+ * time. The z
  * expansion and the contiguous-axis forward pass have a third that runs one z
  * row per group of warp lanes without block-wide barriers (power-of-two
  * N <= 512; other sizes run variant 0 when it is chosen); the z expansion's
@@ -363,7 +366,7 @@ gridspt_status gridspt_multi_destroy(gridspt_multi multi);
  * bytes, contents overwritten) with CUDA events on `stream`, keeps the fastest
  * in the plan and writes the choices to choices_out (host int32[5], may be
  * NULL). It synchronises `stream`. gridspt_set_tuning / gridspt_get_tuning
- * store and read the choices (0 or 1; 0..4 for pass 2; 0..2 for passes 3 and 4), e.g.
+ * store and read the choices (0 or 1; 0..3 for pass 1; 0..6 for pass 2; 0..2 for passes 3 and 4), e.g.
  * from a cache kept by the caller.
  * Results are bitwise identical for all variants: they only change how
  * columns and rows are grouped into thread blocks and warps. */

@@ -1274,12 +1274,14 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
         expansion_codes(2, xa, ya, za);
         switch (pass) {
             case TV_COLPASS: return launch_colpass_fwd(g, f0, F, 2, 1, 0, -1, s);
-            case TV_XEXP:
+            case TV_XEXP:   // forward first, as every x pass of orders >= 2
                 xa.src0 = f0;
                 xa.src1 = f0 + F;
                 xa.out = f0 + 2 * F;
                 xa.out_stride = F;
                 xa.s2_nl = -1;
+                xa.fwd_first = 1;
+                xa.zero_k0 = 1;
                 return launch_xexp(g, xa, s);
             case TV_YEXP:
                 ya.in = f0;

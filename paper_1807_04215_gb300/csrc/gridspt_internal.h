@@ -40,13 +40,16 @@ struct Geo {
 
 // number of tile variants per pass (the autotuner times each; results are
 // bitwise equal across them):
-//   column pass, x expansion: 0 wide tile, 1 narrow tile;
+//   column pass: 0 wide tile, 1 narrow tile;
+//   x expansion: 0 wide tile, 1 narrow tile, 2 narrow and 3 wide tile with
+//                two outputs per transform (fft_column_pair);
 //   y expansion: 0, 1 tiles, 2 TMA-staged tiles, 3 two columns per thread,
-//                4 narrow tile with cp.async prefetch of the next input;
+//                4 narrow tile with cp.async prefetch of the next input,
+//                5 narrow and 6 wide tile with two outputs per transform;
 //   z expansion (and the fused pair products, bispectrum z pass): 0 tile,
 //                1 tile with cp.async prefetch, 2 warp rows;
 //   z forward pass: 0, 1 tiles, 2 warp rows.
-constexpr int kTuneVariants[TV_COUNT] = {2, 2, 5, 3, 3};
+constexpr int kTuneVariants[TV_COUNT] = {2, 4, 7, 3, 3};
 
 // Unit of the wavevector in the derivative multipliers of the expansion
 // passes: k_F, i.e. integer wavevectors s. Every source term of Eq.

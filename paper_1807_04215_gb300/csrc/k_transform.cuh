@@ -249,7 +249,11 @@ __host__ __device__ constexpr int xexp_min_blocks() {
 // fields V_x, V_y, V_z, S are transformed forward along x and combined into
 // A = i k . V, B = -(k^2 / 2) S, delta = cdA A + cdB B, theta = ctA A + ctB B
 // (written to src0, src1 and finalised like MODE 1).
-template <int N, int TZ, int MODE>
+// PAIR: consecutive outputs (and the two forward inputs) are transformed two
+// at a time by fft_column_pair (shared twiddle loads and barriers, 16-byte
+// exchanges of both transforms' elements; the exchange buffer is twice as
+// large). Per output the arithmetic is that of fft_column, bit for bit.
+template <int N, int TZ, int MODE, bool PAIR = false>
 __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __restrict__ twg, float kF,
                                           float inv_kF2, int bx, int by, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
@@ -309,8 +313,23 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
     }
     if constexpr (MODE >= 1) {
         if constexpr (MODE == 1) {
-            fft_column<N, -1, N>(xd, p, buf + c, TZ, tw);
-            if (two) fft_column<N, -1, N>(xt, p, buf + c, TZ, tw);
+            if (PAIR && two) {
+                float2 w[2][E];
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    w[0][i] = xd[i];
+                    w[1][i] = xt[i];
+                }
+                fft_column_pair<N, -1, N>(w, p, reinterpret_cast<float4*>(buf) + c, TZ, tw);
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    xd[i] = w[0][i];
+                    xt[i] = w[1][i];
+                }
+            } else {
+                fft_column<N, -1, N>(xd, p, buf + c, TZ, tw);
+                if (two) fft_column<N, -1, N>(xt, p, buf + c, TZ, tw);
+            }
         }
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -331,10 +350,10 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             }
         }
     }
-    for (int f = 0; f < args.nout; ++f) {
+    // output f before its transform: kx^a * src (or a shell mask times src)
+    auto input = [&](int f, float2 (&y)[E]) {
         const int code = args.codes[f];
         const int kind = code & 15, pa = (code >> 4) & 3, src = (code >> 8) & 3;
-        float2 y[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int n = p + P * i;
@@ -361,20 +380,38 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             }
             y[i] = v;
         }
-        fft_column<N, +1, N>(y, p, buf + c, TZ, tw);
+    };
+    auto store = [&](int f, const float2 (&y)[E]) {
         if (act) {
             float2* o = args.out + f * args.out_stride + colofs;
 #pragma unroll
             for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
         }
+    };
+    for (int f = 0; f < args.nout;) {
+        if (PAIR && f + 1 < args.nout) {
+            float2 y[2][E];
+            input(f, y[0]);
+            input(f + 1, y[1]);
+            fft_column_pair<N, +1, N>(y, p, reinterpret_cast<float4*>(buf) + c, TZ, tw);
+            store(f, y[0]);
+            store(f + 1, y[1]);
+            f += 2;
+        } else {
+            float2 y[E];
+            input(f, y);
+            fft_column<N, +1, N>(y, p, buf + c, TZ, tw);
+            store(f, y);
+            f += 1;
+        }
     }
 }
 
-template <int N, int TZ, int MODE>
-__global__ void __launch_bounds__(TZ * Cfg<N>::PC, xexp_min_blocks<N, TZ, MODE>())
+template <int N, int TZ, int MODE, bool PAIR>
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC, PAIR ? 1 : xexp_min_blocks<N, TZ, MODE>())
 k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
-    extern __shared__ float2 sm[];
-    xexp_body<N, TZ, MODE>(args, twg, kF, inv_kF2, blockIdx.x, blockIdx.y, sm);
+    extern __shared__ __align__(16) float2 sm[];
+    xexp_body<N, TZ, MODE, PAIR>(args, twg, kF, inv_kF2, blockIdx.x, blockIdx.y, sm);
 }
 
 // ------------------------------------------------------------ y expansion
@@ -386,7 +423,9 @@ k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
 // PF: the next input's column tile is copied into a second shared buffer by
 // cp.async (8-byte, zero-filled where the band excludes it) while the outputs
 // of the current input are transformed.
-template <int N, int TZ, bool PF>
+// PAIR: two consecutive outputs of the same input are transformed together by
+// fft_column_pair (as in xexp_body; bit for bit the same outputs).
+template <int N, int TZ, bool PF, bool PAIR = false>
 __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* __restrict__ twg, float kF, int bx,
                                           int by, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
@@ -442,6 +481,29 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
                 }
             }
         }
+        if (PAIR && f + 1 < args.nout && (args.codes[f + 1] & 255) == in) {
+            const int code1 = args.codes[f + 1];
+            const int pb1 = (code1 >> 8) & 3, slot1 = code1 >> 16;
+            float2 y[2][E];
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const float ky = kF * (float)signed_idx(p + P * i, N);
+                y[0][i] = pb == 0 ? xin[i] : cscale(xin[i], pb == 1 ? ky : ky * ky);
+                y[1][i] = pb1 == 0 ? xin[i] : cscale(xin[i], pb1 == 1 ? ky : ky * ky);
+            }
+            fft_column_pair<N, +1, N>(y, p, reinterpret_cast<float4*>(buf) + c, TZ, tw);
+            if (act) {
+                float2* o0 = args.out + slot * args.out_stride + colofs;
+                float2* o1 = args.out + slot1 * args.out_stride + colofs;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    o0[(p + P * i) * estride] = y[0][i];
+                    o1[(p + P * i) * estride] = y[1][i];
+                }
+            }
+            ++f;                                  // the pair's second output is done too
+            continue;
+        }
         float2 y[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -457,11 +519,11 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
     }
 }
 
-template <int N, int TZ, bool PF>
+template <int N, int TZ, bool PF, bool PAIR>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PC)
 k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
-    extern __shared__ float2 sm[];
-    yexp_body<N, TZ, PF>(args, twg, kF, blockIdx.x, blockIdx.y, sm);
+    extern __shared__ __align__(16) float2 sm[];
+    yexp_body<N, TZ, PF, PAIR>(args, twg, kF, blockIdx.x, blockIdx.y, sm);
 }
 
 // Column-pair form of k_yexp: each thread holds two adjacent kz columns, so
@@ -1435,24 +1497,26 @@ struct Launch {
         k_zr2c<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(in, out, fs, g.tw, scale);
         return cudaGetLastError();
     }
+    template <bool PAIR = false>
     static cudaError_t xexp(const Geo& g, const XExpArgs& a, cudaStream_t s) {
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, B ? 2 * B - 1 : N);
-        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
+        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PAIR ? 2 : 1));
         const float kF = kDerivUnit, ikF2 = 1.0f / (kDerivUnit * kDerivUnit);
         cudaError_t e;
         if (a.fwd_first && a.div_in) {
-            e = set_smem(k_xexp<N, TZC, 2>, smem);
+            e = set_smem(k_xexp<N, TZC, 2, false>, sizeof(float2) * (N + (size_t)N * TZC));
             if (e != cudaSuccess) return e;
-            k_xexp<N, TZC, 2><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+            k_xexp<N, TZC, 2, false><<<grid, TZC * PC, sizeof(float2) * (N + (size_t)N * TZC), s>>>(a, g.tw, kF,
+                                                                                                     ikF2);
         } else if (a.fwd_first) {
-            e = set_smem(k_xexp<N, TZC, 1>, smem);
+            e = set_smem(k_xexp<N, TZC, 1, PAIR>, smem);
             if (e != cudaSuccess) return e;
-            k_xexp<N, TZC, 1><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+            k_xexp<N, TZC, 1, PAIR><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
         } else {
-            e = set_smem(k_xexp<N, TZC, 0>, smem);
+            e = set_smem(k_xexp<N, TZC, 0, PAIR>, smem);
             if (e != cudaSuccess) return e;
-            k_xexp<N, TZC, 0><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
+            k_xexp<N, TZC, 0, PAIR><<<grid, TZC * PC, smem, s>>>(a, g.tw, kF, ikF2);
         }
         return cudaGetLastError();
     }
@@ -1465,14 +1529,15 @@ struct Launch {
         k_yexp2<N, TZC><<<grid, TZC / 2 * PC, smem, s>>>(a, g.tw, kDerivUnit);
         return cudaGetLastError();
     }
-    template <bool PF = false>
+    template <bool PF = false, bool PAIR = false>
     static cudaError_t yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
+        static_assert(!(PF && PAIR), "prefetching and paired outputs are separate variants");
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, N);
-        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PF ? 2 : 1));
-        cudaError_t e = set_smem(k_yexp<N, TZC, PF>, smem);
+        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PF || PAIR ? 2 : 1));
+        cudaError_t e = set_smem(k_yexp<N, TZC, PF, PAIR>, smem);
         if (e != cudaSuccess) return e;
-        k_yexp<N, TZC, PF><<<grid, TZC * PC, smem, s>>>(a, g.tw, kDerivUnit);
+        k_yexp<N, TZC, PF, PAIR><<<grid, TZC * PC, smem, s>>>(a, g.tw, kDerivUnit);
         return cudaGetLastError();
     }
     template <bool PF>
@@ -1621,16 +1686,20 @@ struct Launch {
     }                                                                                                      \
     cudaError_t transform_xexp_##N(const Geo& g, const XExpArgs& a, int v, cudaStream_t s) {               \
         if (a.fwd_first && a.div_in) /* four input columns in registers: the narrower tile */              \
-            return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::xexp(g, a, s);                                   \
-        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::xexp(g, a, s)                                    \
-                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::xexp(g, a, s);                                   \
+            return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template xexp<false>(g, a, s);                   \
+        if (v == 2) return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template xexp<true>(g, a, s);            \
+        if (v == 3) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template xexp<true>(g, a, s);            \
+        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template xexp<false>(g, a, s)                    \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template xexp<false>(g, a, s);                   \
     }                                                                                                      \
     cudaError_t transform_yexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
         if (v == 2 && N >= 128 && a.band <= 0) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp_tma(g, a, s); \
         if (v == 3) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::yexp2(g, a, s);                          \
-        if (v == 4) return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<true>(g, a, s);             \
-        return v == 1 ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<false>(g, a, s)               \
-                      : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template yexp<false>(g, a, s);              \
+        if (v == 4) return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<true, false>(g, a, s);      \
+        if (v == 5) return Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<false, true>(g, a, s);      \
+        if (v == 6) return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template yexp<false, true>(g, a, s);      \
+        return v == 1 ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::template yexp<false, false>(g, a, s)        \
+                      : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::template yexp<false, false>(g, a, s);       \
     }                                                                                                      \
     cudaError_t transform_zexp_##N(const Geo& g, const YZExpArgs& a, int v, cudaStream_t s) {              \
         if (a.band & 1) return cudaErrorInvalidValue; /* row copies move kz pairs */                       \
