@@ -30,13 +30,12 @@ METRIC = "Mcells*orders/s to 5th order at 512^3 FP32"
 UNIT = "Mcells*orders/s"
 N_GRID, BOX, N_MAX = 512, 2000.0, 5
 FALLBACK_HBM_GBS = 6800.0
-# DRAM traffic / algorithmic bytes measured by ncu for the kernels as they stand
-# (captures of the y expansion at 512^3, one field per launch, and of the
-# warp-row z expansion, the four launches of one realisation at 256^3, bytes
-# growing as N^3); traffic per launch is reported as this ratio times the
-# launch's algorithmic bytes. A kernel changed since its capture has no entry
-# (traffic null).
-NCU_TRAFFIC_RATIO = {"y_expand": 0.969, "z_expand": 1.008}
+# DRAM traffic / algorithmic bytes measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) for the kernels as they stand, on the launches of one
+# realisation of this workload (512^3); traffic per launch is reported as this
+# ratio times the launch's algorithmic bytes. A kernel changed since its
+# capture has no entry (traffic null).
+NCU_TRAFFIC_RATIO = {"z_expand": 1.007, "y_expand": 1.12, "x_fwd_expand": 1.046}
 
 
 def log_edges(lo, hi, nb):
