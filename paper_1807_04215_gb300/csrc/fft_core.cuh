@@ -22,13 +22,58 @@
 namespace gridspt {
 
 // ----------------------------------------------------------- complex helpers
+// The real and imaginary parts are combined with the packed two-lane FP32
+// instructions of sm_100 and later (add/sub/mul/fma .rn .f32x2): each lane is
+// rounded exactly as the scalar instruction would round it, so the results are
+// those of the scalar forms below, with half the arithmetic instructions.
+#ifndef GRIDSPT_PACKED_F32X2
+#define GRIDSPT_PACKED_F32X2 1
+#endif
+#if GRIDSPT_PACKED_F32X2
+__device__ __forceinline__ unsigned long long f2u(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 u2f(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(make_float2(s, s))));
+    return u2f(r);
+}
+// (a.x b.x - a.y b.y, a.x b.y + a.y b.x): t = (a.y b.y, a.y b.x) rounded, then
+// fma((a.x, a.x), (b.x, b.y), (-t.x, t.y)), as the scalar form
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    unsigned long long t, r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(f2u(make_float2(a.y, a.y))), "l"(f2u(make_float2(b.y, b.x))));
+    const float2 tf = u2f(t);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r)
+        : "l"(f2u(make_float2(a.x, a.x))), "l"(f2u(b)), "l"(f2u(make_float2(-tf.x, tf.y))));
+    return u2f(r);
+}
+#else
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+#endif
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 // multiply by DIR * i
 template <int DIR>
 __device__ __forceinline__ float2 cmul_i(float2 a) {
