@@ -409,4 +409,182 @@ __device__ __forceinline__ void fft_column_pair(float2 (&x)[2][fft_elems(L)], in
     fft_stages_pair<L, 0, DIR, N>(x, p, col, SN, tw);
 }
 
+
+// ------------------------------------------------ column-pass variant (fft_col)
+// The column transform of the column passes (colpass, x and y expansion), with
+//  * NB = 2 exchange buffers used in turn (stage S writes buffer S % 2): a
+//    buffer is rewritten only after a later block barrier that every reader of
+//    its previous contents has passed, so each exchange takes one barrier
+//    instead of two. A transform with an odd number of exchanges ends with a
+//    barrier, so back-to-back transforms keep the alternation safe. NB = 1:
+//    one buffer and two barriers per exchange, as fft_column.
+//  * a padded exchange layout: element n of a column at col_row(n) * SN, one
+//    padding row per 8 rows. The scatter of a radix-8 stage by a warp that
+//    spans several butterflies of a narrow tile then hits distinct banks.
+//  * the lane-major stage-twiddle table of fft_row, twl[j * P + p] (filled by
+//    col_twiddles): the P-indexed twiddle loads of a warp read consecutive
+//    entries instead of entries t * k * TWS apart.
+// Butterfly arithmetic and twiddle values are those of fft_stage, so results
+// are bitwise equal to fft_column.
+__host__ __device__ constexpr int col_rows(int L) { return L + L / 8; }
+__device__ __forceinline__ int col_row(int n) { return n + (n >> 3); }
+
+// Fill the lane-major stage-twiddle table of a length-L column transform from
+// the table of N-th roots (global or shared); threads p < P of the block each
+// fill their own entries. The caller orders the table before its first use by
+// a block barrier (the first exchange of fft_col has one before any stage
+// that reads twiddles).
+template <int L, int N>
+__device__ __forceinline__ void col_twiddles(float2* twl, const float2* tw) {
+    constexpr int P = L / fft_elems(L);
+    if (threadIdx.x < P) fft_row_twiddles<L, N>(twl, tw, threadIdx.x);
+}
+
+template <int L, int S, int DIR, int NB>
+__device__ __forceinline__ void fft_col_stage(float2 (&x)[fft_elems(L)], int p, float2* colA, float2* colB, int SN,
+                                              const float2* __restrict__ twl) {
+    constexpr int E = fft_elems(L);
+    constexpr int P = L / E;
+    constexpr int R = fft_radix(L, S);
+    constexpr int Ls = fft_ls(L, S);
+    constexpr int Q = E / R;
+    constexpr bool last = (S == fft_nstages(L) - 1);
+    constexpr int J0 = fft_row_tw_count<L>(S);
+    float2* col = (NB == 2 && (S & 1)) ? colB : colA;
+    float2 y[E];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 v[R];
+        const int b = p + q * P;
+        const int k = (Ls == 1) ? 0 : (b % Ls);
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = x[q + t * Q];
+        if constexpr (Ls > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w = twl[(J0 + q * (R - 1) + (t - 1)) * P + p];
+                if (DIR < 0) w.y = -w.y;
+                v[t] = cmul(v[t], w);
+            }
+        }
+        dft_small<R, DIR>(v);
+        if constexpr (last) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) y[q + t * Q] = v[t];
+        } else {
+            const int base = (b / Ls) * Ls * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) col[col_row(base + t * Ls) * SN] = v[t];
+        }
+    }
+    if constexpr (last) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = y[i];
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = col[col_row(p + P * i) * SN];
+        if constexpr (NB == 1) __syncthreads();
+    }
+}
+
+template <int L, int S, int DIR, int NB>
+__device__ __forceinline__ void fft_col_stages(float2 (&x)[fft_elems(L)], int p, float2* colA, float2* colB, int SN,
+                                               const float2* __restrict__ twl) {
+    if constexpr (S < fft_nstages(L)) {
+        fft_col_stage<L, S, DIR, NB>(x, p, colA, colB, SN, twl);
+        fft_col_stages<L, S + 1, DIR, NB>(x, p, colA, colB, SN, twl);
+    }
+}
+
+// Every thread of the block must call it the same number of times.
+template <int L, int DIR, int NB>
+__device__ __forceinline__ void fft_col(float2 (&x)[fft_elems(L)], int p, float2* colA, float2* colB, int SN,
+                                        const float2* __restrict__ twl) {
+    fft_col_stages<L, 0, DIR, NB>(x, p, colA, colB, SN, twl);
+    if constexpr (NB == 2 && (fft_nstages(L) - 1) % 2 == 1) __syncthreads();
+}
+
+// Two columns per thread (the layout of fft_column_pair: 16-byte elements),
+// same buffers, barriers and twiddle table as fft_col.
+template <int L, int S, int DIR, int NB>
+__device__ __forceinline__ void fft_col_pair_stage(float2 (&x)[2][fft_elems(L)], int p, float4* colA, float4* colB,
+                                                   int SN, const float2* __restrict__ twl) {
+    constexpr int E = fft_elems(L);
+    constexpr int P = L / E;
+    constexpr int R = fft_radix(L, S);
+    constexpr int Ls = fft_ls(L, S);
+    constexpr int Q = E / R;
+    constexpr bool last = (S == fft_nstages(L) - 1);
+    constexpr int J0 = fft_row_tw_count<L>(S);
+    float4* col = (NB == 2 && (S & 1)) ? colB : colA;
+    float2 y[2][E];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 v0[R], v1[R];
+        const int b = p + q * P;
+        const int k = (Ls == 1) ? 0 : (b % Ls);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            v0[t] = x[0][q + t * Q];
+            v1[t] = x[1][q + t * Q];
+        }
+        if constexpr (Ls > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w = twl[(J0 + q * (R - 1) + (t - 1)) * P + p];
+                if (DIR < 0) w.y = -w.y;
+                v0[t] = cmul(v0[t], w);
+                v1[t] = cmul(v1[t], w);
+            }
+        }
+        dft_small<R, DIR>(v0);
+        dft_small<R, DIR>(v1);
+        if constexpr (last) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                y[0][q + t * Q] = v0[t];
+                y[1][q + t * Q] = v1[t];
+            }
+        } else {
+            const int base = (b / Ls) * Ls * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                col[col_row(base + t * Ls) * SN] = make_float4(v0[t].x, v0[t].y, v1[t].x, v1[t].y);
+        }
+    }
+    if constexpr (last) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            x[0][i] = y[0][i];
+            x[1][i] = y[1][i];
+        }
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float4 u = col[col_row(p + P * i) * SN];
+            x[0][i] = make_float2(u.x, u.y);
+            x[1][i] = make_float2(u.z, u.w);
+        }
+        if constexpr (NB == 1) __syncthreads();
+    }
+}
+
+template <int L, int S, int DIR, int NB>
+__device__ __forceinline__ void fft_col_pair_stages(float2 (&x)[2][fft_elems(L)], int p, float4* colA, float4* colB,
+                                                    int SN, const float2* __restrict__ twl) {
+    if constexpr (S < fft_nstages(L)) {
+        fft_col_pair_stage<L, S, DIR, NB>(x, p, colA, colB, SN, twl);
+        fft_col_pair_stages<L, S + 1, DIR, NB>(x, p, colA, colB, SN, twl);
+    }
+}
+
+template <int L, int DIR, int NB>
+__device__ __forceinline__ void fft_col_pair(float2 (&x)[2][fft_elems(L)], int p, float4* colA, float4* colB,
+                                             int SN, const float2* __restrict__ twl) {
+    fft_col_pair_stages<L, 0, DIR, NB>(x, p, colA, colB, SN, twl);
+    if constexpr (NB == 2 && (fft_nstages(L) - 1) % 2 == 1) __syncthreads();
+}
+
 }  // namespace gridspt

@@ -62,7 +62,10 @@ template <int N>
 __host__ __device__ constexpr int qtz() { return kQueueThreads / (N / fft_elems(N)); }
 
 template <int N>
-__host__ __device__ constexpr size_t col_smem() { return sizeof(float2) * (N + (size_t)N * qtz<N>()); }
+__host__ __device__ constexpr size_t col_smem() {
+    return ColSm<N, qtz<N>()>::bytes > colpass_smem<N, qtz<N>()>() ? ColSm<N, qtz<N>()>::bytes
+                                                                    : colpass_smem<N, qtz<N>()>();
+}
 
 template <int N>
 __device__ __forceinline__ void q_tables(float2* twl, float2* twp, const float2* __restrict__ twg) {
@@ -242,10 +245,12 @@ __device__ void q_zr2c(const QStage& st, long long tile, float2* sm, bool table_
 }
 
 // Layout class of the table a stage kind keeps at the start of shared memory:
-// 1 the column table of the transforms, 2 the warp-row tables of k_zrow, 3 the
-// warp-row tables of QRow (0: none).
+// 1 the stage-twiddle table of the expansion column transforms (fft_col),
+// 2 the warp-row tables of k_zrow, 3 the warp-row tables of QRow, 4 the table
+// of N-th roots of the forward column passes (0: none).
 __host__ __device__ constexpr int q_table_class(int kind, bool row_ok) {
-    return (kind == Q_XEXP0 || kind == Q_XEXP1 || kind == Q_YEXP || kind == Q_COLY || kind == Q_COLX) ? 1
+    return (kind == Q_XEXP0 || kind == Q_XEXP1 || kind == Q_YEXP) ? 1
+           : (kind == Q_COLY || kind == Q_COLX) ? 4
            : kind == Q_Z ? (row_ok ? 2 : 3) : kind == Q_ZR2C ? 3 : 0;
 }
 

@@ -58,6 +58,38 @@ struct Cfg {
     static_assert(pair_smem(TZP) <= 232448, "fused z pass tiles exceed shared memory");
 };
 
+// Shared memory of the column passes (colpass, x and y expansion): the
+// lane-major stage-twiddle table of fft_col, then NB exchange buffers of
+// col_rows(N) rows of TZ columns (W = 2: column pairs, 16-byte elements), then
+// EXTRA float2 (the y pass's prefetch tile). Two buffers (one barrier per
+// exchange) whenever they fit the 227 KB a block may hold; a variant whose
+// tiles do not fit even with one buffer (the wide column-pair tile of N = 768)
+// is not built for that size.
+template <int N, int TZ, int W = 1, int EXTRA = 0>
+struct ColSm {
+    static constexpr int P = N / fft_elems(N);
+    static constexpr int TW = (fft_row_tw_total<N>() * P + 1) / 2 * 2;   // 16-byte multiple
+    static constexpr int BUF = col_rows(N) * TZ * W;
+    static constexpr size_t bytes_nb(int nb) { return sizeof(float2) * (TW + (size_t)nb * BUF + EXTRA); }
+    static constexpr bool fits = bytes_nb(1) <= 232448;
+    static constexpr int NB = bytes_nb(2) <= 232448 ? 2 : 1;
+    static constexpr size_t bytes = bytes_nb(NB);
+};
+
+// Shared memory of the forward column pass (one transform per block, so the
+// plain fft_column with one exchange buffer and the table of N-th roots).
+template <int N, int TZ>
+__host__ __device__ constexpr size_t colpass_smem() { return sizeof(float2) * (N + (size_t)N * TZ); }
+
+// Blocks per SM the expansion column passes are compiled for: two 512-thread
+// blocks (64 registers a thread) for the narrow tile of power-of-two N >= 512,
+// where one block of the natural ~75-86 registers leaves 16 warps per SM; one
+// elsewhere (smaller N and radix-3 sizes would spill heavily).
+template <int N, int TZ>
+__host__ __device__ constexpr int col_min_blocks() {
+    return (fft_elems(N) == 8 && N >= 512 && TZ * (N / fft_elems(N)) <= 512) ? 2 : 1;
+}
+
 __device__ __forceinline__ int signed_idx(int n, int N) { return n < N / 2 ? n : n - N; }
 
 __device__ __forceinline__ void load_table(float2* tw, const float2* __restrict__ twg, int N) {
@@ -228,13 +260,11 @@ k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restric
 }
 
 // ------------------------------------------------------------ x expansion
-// Blocks per SM the x pass is compiled for: two 512-thread blocks (64
-// registers a thread, a small spill) for the narrow tile of power-of-two
-// N >= 512, where one block of the natural ~86 registers leaves 16 warps per
-// SM; one elsewhere (smaller N and radix-3 sizes would spill heavily).
+// Blocks per SM: col_min_blocks (a small spill at 64 registers), except for
+// the divergence form, which keeps four input columns in registers.
 template <int N, int TZ, int MODE>
 __host__ __device__ constexpr int xexp_min_blocks() {
-    return (MODE != 2 && fft_elems(N) == 8 && N >= 512 && TZ * Cfg<N>::PC <= 512) ? 2 : 1;
+    return MODE != 2 ? col_min_blocks<N, TZ>() : 1;
 }
 
 // Inputs: delta(k) and theta(k) columns along kx. Each output f is
@@ -257,10 +287,15 @@ template <int N, int TZ, int MODE, bool PAIR = false>
 __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __restrict__ twg, float kF,
                                           float inv_kF2, int bx, int by, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
-    float2* tw = sm;
-    float2* buf = sm + N;
+    using CS = ColSm<N, TZ, PAIR ? 2 : 1>;
+    constexpr int NB = CS::NB;
+    float2* twl = sm;
+    float2* bufA = sm + CS::TW;
+    float2* bufB = bufA + CS::BUF;
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    if (!table_ready) load_table(tw, twg, N);
+    float4* pairA = reinterpret_cast<float4*>(bufA) + c;
+    float4* pairB = reinterpret_cast<float4*>(bufB) + c;
+    if (!table_ready) col_twiddles<N, N>(twl, twg);
     const int kz = bx * TZ + c;
     const int B = args.band;
     const int ky = (B > 0 && by >= B) ? N - (2 * B - 1 - by) : by;   // band rows: [0, B) and (N - B, N)
@@ -271,8 +306,18 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
     float2 xd[E], xt[E];
     const int sy = signed_idx(ky, N), sz = kz;
     const int syz = sy * sy + sz * sz;
+    // column `base` of this thread (MODE 0: with the cut on delta_1)
+    auto load_col = [&](const float2* base, float2 (&v)[E]) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            v[i] = act ? base[colofs + (p + P * i) * estride] : make_float2(0.f, 0.f);
+            if (MODE == 0 && args.s2_in >= 0) {
+                const int sx = signed_idx(p + P * i, N);
+                if ((long long)(sx * sx + syz) > args.s2_in) v[i] = make_float2(0.f, 0.f);
+            }
+        }
+    };
     if constexpr (MODE == 2) {
-        __syncthreads();                                  // twiddle table loaded
         float2 A[E], Bs[E];
 #pragma unroll 1
         for (int q = 0; q < 4; ++q) {
@@ -280,7 +325,7 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             float2 v[E];
 #pragma unroll
             for (int i = 0; i < E; ++i) v[i] = act ? col[(p + P * i) * estride] : make_float2(0.f, 0.f);
-            fft_column<N, -1, N>(v, p, buf + c, TZ, tw);
+            fft_col<N, -1, NB>(v, p, bufA + c, bufB + c, TZ, twl);
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int sx = signed_idx(p + P * i, N);
@@ -299,17 +344,14 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             xd[i] = make_float2(fmaf(args.cdA, A[i].x, args.cdB * Bs[i].x), fmaf(args.cdA, A[i].y, args.cdB * Bs[i].y));
             xt[i] = make_float2(fmaf(args.ctA, A[i].x, args.ctB * Bs[i].x), fmaf(args.ctA, A[i].y, args.ctB * Bs[i].y));
         }
-    } else {
+    } else if constexpr (MODE == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             xd[i] = act ? args.src0[colofs + (p + P * i) * estride] : make_float2(0.f, 0.f);
             xt[i] = (act && two) ? args.src1[colofs + (p + P * i) * estride] : xd[i];
-            if (MODE == 0 && args.s2_in >= 0) {          // the cut on delta_1
-                const int sx = signed_idx(p + P * i, N);
-                if ((long long)(sx * sx + syz) > args.s2_in) xd[i] = xt[i] = make_float2(0.f, 0.f);
-            }
         }
-        __syncthreads();
+    } else {
+        load_col(args.src0, xd);                          // theta is read when its outputs start
     }
     if constexpr (MODE >= 1) {
         if constexpr (MODE == 1) {
@@ -320,15 +362,15 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
                     w[0][i] = xd[i];
                     w[1][i] = xt[i];
                 }
-                fft_column_pair<N, -1, N>(w, p, reinterpret_cast<float4*>(buf) + c, TZ, tw);
+                fft_col_pair<N, -1, NB>(w, p, pairA, pairB, TZ, twl);
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     xd[i] = w[0][i];
                     xt[i] = w[1][i];
                 }
             } else {
-                fft_column<N, -1, N>(xd, p, buf + c, TZ, tw);
-                if (two) fft_column<N, -1, N>(xt, p, buf + c, TZ, tw);
+                fft_col<N, -1, NB>(xd, p, bufA + c, bufB + c, TZ, twl);
+                if (two) fft_col<N, -1, NB>(xt, p, bufA + c, bufB + c, TZ, twl);
             }
         }
 #pragma unroll
@@ -350,8 +392,14 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             }
         }
     }
-    // output f before its transform: kx^a * src (or a shell mask times src)
-    auto input = [&](int f, float2 (&y)[E]) {
+    // Outputs. One source column is held in registers at a time: delta for the
+    // leading delta outputs, then theta for the rest (phi = theta / k^2 is formed
+    // per element). Theta is read from memory when its outputs start: MODE 0
+    // reads the input, MODES 1 and 2 re-read the finalised column this thread
+    // stored above (its own stores, so the values are those it held).
+    // output f before its transform: kx^a * src (or a shell mask times src),
+    // src taken from the column sc (delta or theta)
+    auto input = [&](int f, const float2 (&sc)[E], float2 (&y)[E]) {
         const int code = args.codes[f];
         const int kind = code & 15, pa = (code >> 4) & 3, src = (code >> 8) & 3;
 #pragma unroll
@@ -360,13 +408,11 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             const int sx = signed_idx(n, N);
             const int s2 = sx * sx + syz;
             float2 v;
-            if (src == XS_DELTA) {
-                v = xd[i];
-            } else if (src == XS_THETA) {
-                v = xt[i];
+            if (src == XS_DELTA || src == XS_THETA) {
+                v = sc[i];
             } else if (src == XS_PHI) {
                 const float g = s2 ? inv_kF2 / (float)s2 : 0.f;   // 1 / k^2, 0 at k = 0
-                v = cscale(xt[i], g);
+                v = cscale(sc[i], g);
             } else {
                 v = make_float2(1.f, 0.f);
             }
@@ -388,28 +434,50 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
         }
     };
-    for (int f = 0; f < args.nout;) {
-        if (PAIR && f + 1 < args.nout) {
+    auto is_delta = [&](int f) { return ((args.codes[f] >> 8) & 3) == XS_DELTA; };
+    // transform and store outputs f (and f + 1 when paired) from column sc
+    auto emit = [&](int f, bool pair, const float2 (&sc)[E]) {
+        if (PAIR && pair) {
             float2 y[2][E];
-            input(f, y[0]);
-            input(f + 1, y[1]);
-            fft_column_pair<N, +1, N>(y, p, reinterpret_cast<float4*>(buf) + c, TZ, tw);
+            input(f, sc, y[0]);
+            input(f + 1, sc, y[1]);
+            fft_col_pair<N, +1, NB>(y, p, pairA, pairB, TZ, twl);
             store(f, y[0]);
             store(f + 1, y[1]);
-            f += 2;
         } else {
             float2 y[E];
-            input(f, y);
-            fft_column<N, +1, N>(y, p, buf + c, TZ, tw);
+            input(f, sc, y);
+            fft_col<N, +1, NB>(y, p, bufA + c, bufB + c, TZ, twl);
             store(f, y);
-            f += 1;
+        }
+    };
+    int f = 0;
+    while (f < args.nout && is_delta(f)) {
+        const bool pair = PAIR && f + 1 < args.nout && is_delta(f + 1);
+        emit(f, pair, xd);
+        f += pair ? 2 : 1;
+    }
+    if (f < args.nout) {
+        float2 xs[E];
+        load_col(two ? args.src1 : args.src0, xs);
+        while (f < args.nout) {
+            if (is_delta(f)) {                            // a later delta output: re-read delta
+                float2 d[E];
+                load_col(args.src0, d);
+                emit(f, false, d);
+                f += 1;
+                continue;
+            }
+            const bool pair = PAIR && f + 1 < args.nout && !is_delta(f + 1);
+            emit(f, pair, xs);
+            f += pair ? 2 : 1;
         }
     }
 }
 
 template <int N, int TZ, int MODE, bool PAIR>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PC, PAIR ? 1 : xexp_min_blocks<N, TZ, MODE>())
-k_xexp(XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
+k_xexp(const __grid_constant__ XExpArgs args, const float2* __restrict__ twg, float kF, float inv_kF2) {
     extern __shared__ __align__(16) float2 sm[];
     xexp_body<N, TZ, MODE, PAIR>(args, twg, kF, inv_kF2, blockIdx.x, blockIdx.y, sm);
 }
@@ -429,11 +497,14 @@ template <int N, int TZ, bool PF, bool PAIR = false>
 __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* __restrict__ twg, float kF, int bx,
                                           int by, float2* sm, bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
-    float2* tw = sm;
-    float2* buf = sm + N;
-    float2* pre = buf + N * TZ;                  // PF: next input tile, element (n, c) at n * TZ + c
+    using CS = ColSm<N, TZ, PAIR ? 2 : 1, PF ? N * TZ : 0>;
+    constexpr int NB = CS::NB;
+    float2* twl = sm;
+    float2* bufA = sm + CS::TW;
+    float2* bufB = bufA + CS::BUF;
+    float2* pre = bufA + NB * CS::BUF;           // PF: next input tile, element (n, c) at n * TZ + c
     const int tid = threadIdx.x, c = tid % TZ, p = tid / TZ;
-    if (!table_ready) load_table(tw, twg, N);
+    if (!table_ready) col_twiddles<N, N>(twl, twg);
     const int kz = bx * TZ + c;
     const int xr = by;
     const int B = args.band;
@@ -443,7 +514,6 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
     float2 xin[E];
     int cur = -1;
     bool have_next = false;
-    __syncthreads();
     for (int f = 0; f < args.nout; ++f) {
         const int code = args.codes[f];
         const int in = code & 255, pb = (code >> 8) & 3, slot = code >> 16;
@@ -491,7 +561,8 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
                 y[0][i] = pb == 0 ? xin[i] : cscale(xin[i], pb == 1 ? ky : ky * ky);
                 y[1][i] = pb1 == 0 ? xin[i] : cscale(xin[i], pb1 == 1 ? ky : ky * ky);
             }
-            fft_column_pair<N, +1, N>(y, p, reinterpret_cast<float4*>(buf) + c, TZ, tw);
+            fft_col_pair<N, +1, NB>(y, p, reinterpret_cast<float4*>(bufA) + c, reinterpret_cast<float4*>(bufB) + c,
+                                    TZ, twl);
             if (act) {
                 float2* o0 = args.out + slot * args.out_stride + colofs;
                 float2* o1 = args.out + slot1 * args.out_stride + colofs;
@@ -510,7 +581,7 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
             const float ky = kF * (float)signed_idx(p + P * i, N);
             y[i] = pb == 0 ? xin[i] : cscale(xin[i], pb == 1 ? ky : ky * ky);
         }
-        fft_column<N, +1, N>(y, p, buf + c, TZ, tw);
+        fft_col<N, +1, NB>(y, p, bufA + c, bufB + c, TZ, twl);
         if (act) {
             float2* o = args.out + slot * args.out_stride + colofs;
 #pragma unroll
@@ -520,8 +591,8 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
 }
 
 template <int N, int TZ, bool PF, bool PAIR>
-__global__ void __launch_bounds__(TZ * Cfg<N>::PC)
-k_yexp(YZExpArgs args, const float2* __restrict__ twg, float kF) {
+__global__ void __launch_bounds__(TZ * Cfg<N>::PC, (PF || PAIR) ? 1 : col_min_blocks<N, TZ>())
+k_yexp(const __grid_constant__ YZExpArgs args, const float2* __restrict__ twg, float kF) {
     extern __shared__ __align__(16) float2 sm[];
     yexp_body<N, TZ, PF, PAIR>(args, twg, kF, blockIdx.x, blockIdx.y, sm);
 }
@@ -1054,7 +1125,7 @@ __device__ __forceinline__ void zrow_body(const ZPairArgs& args, const float2* _
 
 template <int N, int NT, bool BAND>
 __global__ void __launch_bounds__(kRowWarps * 32, NT == 0 ? 3 : 2)
-k_zrow(ZPairArgs args, const float2* __restrict__ twg, float kF) {
+k_zrow(const __grid_constant__ ZPairArgs args, const float2* __restrict__ twg, float kF) {
     extern __shared__ __align__(16) float2 sm[];
     zrow_body<N, NT, BAND>(args, twg, kF, (long long)blockIdx.x * kRowWarps, (long long)gridDim.x * kRowWarps, sm);
 }
@@ -1450,7 +1521,7 @@ struct Launch {
     static cudaError_t colpass(const Geo& g, float2* d, long long fs, int count, int axis, int fin,
                                long long s2_nl, cudaStream_t s) {
         dim3 grid((M + TZC - 1) / TZC, N, count);
-        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC);
+        const size_t smem = colpass_smem<N, TZC>();
         cudaError_t e;
 #define GRIDSPT_COL(AX_, FIN_)                                                        \
     e = set_smem(k_colpass<N, TZC, AX_, FIN_>, smem);                                 \
@@ -1499,16 +1570,20 @@ struct Launch {
     }
     template <bool PAIR = false>
     static cudaError_t xexp(const Geo& g, const XExpArgs& a, cudaStream_t s) {
+        if constexpr (!ColSm<N, TZC, PAIR ? 2 : 1>::fits) return cudaErrorNotSupported;
+        else return xexp_fit<PAIR>(g, a, s);
+    }
+    template <bool PAIR>
+    static cudaError_t xexp_fit(const Geo& g, const XExpArgs& a, cudaStream_t s) {
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, B ? 2 * B - 1 : N);
-        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PAIR ? 2 : 1));
+        const size_t smem = ColSm<N, TZC, PAIR ? 2 : 1>::bytes;
         const float kF = kDerivUnit, ikF2 = 1.0f / (kDerivUnit * kDerivUnit);
         cudaError_t e;
         if (a.fwd_first && a.div_in) {
-            e = set_smem(k_xexp<N, TZC, 2, false>, sizeof(float2) * (N + (size_t)N * TZC));
+            e = set_smem(k_xexp<N, TZC, 2, false>, ColSm<N, TZC>::bytes);
             if (e != cudaSuccess) return e;
-            k_xexp<N, TZC, 2, false><<<grid, TZC * PC, sizeof(float2) * (N + (size_t)N * TZC), s>>>(a, g.tw, kF,
-                                                                                                     ikF2);
+            k_xexp<N, TZC, 2, false><<<grid, TZC * PC, ColSm<N, TZC>::bytes, s>>>(a, g.tw, kF, ikF2);
         } else if (a.fwd_first) {
             e = set_smem(k_xexp<N, TZC, 1, PAIR>, smem);
             if (e != cudaSuccess) return e;
@@ -1532,9 +1607,14 @@ struct Launch {
     template <bool PF = false, bool PAIR = false>
     static cudaError_t yexp(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
         static_assert(!(PF && PAIR), "prefetching and paired outputs are separate variants");
+        if constexpr (!ColSm<N, TZC, PAIR ? 2 : 1, PF ? N * TZC : 0>::fits) return cudaErrorNotSupported;
+        else return yexp_fit<PF, PAIR>(g, a, s);
+    }
+    template <bool PF, bool PAIR>
+    static cudaError_t yexp_fit(const Geo& g, const YZExpArgs& a, cudaStream_t s) {
         const int B = a.band > 0 && a.band < M ? a.band : 0;
         dim3 grid(((B ? B : M) + TZC - 1) / TZC, N);
-        const size_t smem = sizeof(float2) * (N + (size_t)N * TZC * (PF || PAIR ? 2 : 1));
+        const size_t smem = ColSm<N, TZC, PAIR ? 2 : 1, PF ? N * TZC : 0>::bytes;
         cudaError_t e = set_smem(k_yexp<N, TZC, PF, PAIR>, smem);
         if (e != cudaSuccess) return e;
         k_yexp<N, TZC, PF, PAIR><<<grid, TZC * PC, smem, s>>>(a, g.tw, kDerivUnit);
