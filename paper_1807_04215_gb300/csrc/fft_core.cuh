@@ -74,6 +74,27 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 #endif
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Lane-wise forms used by the pair products of real fields stored as float2
+// pairs of cells: (a.x b.x, a.y b.y) and (fma(s, v.x, c.x), fma(s, v.y, c.y)),
+// rounded as the scalar instructions.
+#if GRIDSPT_PACKED_F32X2
+__device__ __forceinline__ float2 lmul(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 lfma(float s, float2 v, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(make_float2(s, s))), "l"(f2u(v)), "l"(f2u(c)));
+    return u2f(r);
+}
+#else
+__device__ __forceinline__ float2 lmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 lfma(float s, float2 v, float2 c) {
+    return make_float2(fmaf(s, v.x, c.x), fmaf(s, v.y, c.y));
+}
+#endif
 // multiply by DIR * i
 template <int DIR>
 __device__ __forceinline__ float2 cmul_i(float2 a) {

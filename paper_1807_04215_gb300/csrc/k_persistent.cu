@@ -168,11 +168,9 @@ __device__ void q_zrow(const ZPairArgs& args, const float2* __restrict__ twg, fl
 #pragma unroll
                     for (int i = 0; i < E; ++i) {
                         const float2 gv = pr[p + P * i];
-                        const float2 fg = make_float2(x[i].x * gv.x, x[i].y * gv.y);
-                        accA[t][i].x = fmaf(ca, fg.x, accA[t][i].x);
-                        accA[t][i].y = fmaf(ca, fg.y, accA[t][i].y);
-                        accB[t][i].x = fmaf(cb, fg.x, accB[t][i].x);
-                        accB[t][i].y = fmaf(cb, fg.y, accB[t][i].y);
+                        const float2 fg = lmul(x[i], gv);
+                        accA[t][i] = lfma(ca, fg, accA[t][i]);
+                        accB[t][i] = lfma(cb, fg, accB[t][i]);
                     }
                 }
             }
@@ -189,20 +187,16 @@ __device__ void q_zrow(const ZPairArgs& args, const float2* __restrict__ twg, fl
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     const float2 va = ia[p + P * i], vb = ib[p + P * i];
-                    accA[t][i].x += va.x;
-                    accA[t][i].y += va.y;
-                    accB[t][i].x += vb.x;
-                    accB[t][i].y += vb.y;
+                    accA[t][i] = cadd(accA[t][i], va);
+                    accB[t][i] = cadd(accB[t][i], vb);
                 }
             }
             float2* oa = reinterpret_cast<float2*>(T.out_a) + row * M;
             float2* ob = reinterpret_cast<float2*>(T.out_b) + row * M;
 #pragma unroll
             for (int i = 0; i < E; ++i) {
-                oa[p + P * i] = make_float2(fmaf(T.ca0, accA[t][i].x, T.ca1 * accB[t][i].x),
-                                            fmaf(T.ca0, accA[t][i].y, T.ca1 * accB[t][i].y));
-                ob[p + P * i] = make_float2(fmaf(T.cb0, accA[t][i].x, T.cb1 * accB[t][i].x),
-                                            fmaf(T.cb0, accA[t][i].y, T.cb1 * accB[t][i].y));
+                oa[p + P * i] = lfma(T.ca0, accA[t][i], cscale(accB[t][i], T.ca1));
+                ob[p + P * i] = lfma(T.cb0, accA[t][i], cscale(accB[t][i], T.cb1));
             }
         }
     }

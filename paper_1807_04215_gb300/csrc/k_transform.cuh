@@ -393,12 +393,13 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
         }
     }
     // Outputs. One source column is held in registers at a time: delta for the
-    // leading delta outputs, then theta for the rest (phi = theta / k^2 is formed
-    // per element). Theta is read from memory when its outputs start: MODE 0
-    // reads the input, MODES 1 and 2 re-read the finalised column this thread
-    // stored above (its own stores, so the values are those it held).
+    // leading delta outputs, then theta, then phi = theta / k^2 (converted in
+    // place once, so each element is divided once). Theta is read from memory
+    // when its outputs start: MODE 0 reads the input, MODES 1 and 2 re-read the
+    // finalised column this thread stored above (its own stores, so the values
+    // are those it held).
     // output f before its transform: kx^a * src (or a shell mask times src),
-    // src taken from the column sc (delta or theta)
+    // src (delta, theta or phi) taken from the column sc
     auto input = [&](int f, const float2 (&sc)[E], float2 (&y)[E]) {
         const int code = args.codes[f];
         const int kind = code & 15, pa = (code >> 4) & 3, src = (code >> 8) & 3;
@@ -407,15 +408,8 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             const int n = p + P * i;
             const int sx = signed_idx(n, N);
             const int s2 = sx * sx + syz;
-            float2 v;
-            if (src == XS_DELTA || src == XS_THETA) {
-                v = sc[i];
-            } else if (src == XS_PHI) {
-                const float g = s2 ? inv_kF2 / (float)s2 : 0.f;   // 1 / k^2, 0 at k = 0
-                v = cscale(sc[i], g);
-            } else {
-                v = make_float2(1.f, 0.f);
-            }
+            const float2 v0 = src == XS_ONE ? make_float2(1.f, 0.f) : sc[i];
+            float2 v = v0;
             if (kind == XK_POW) {
                 const float kx = kF * (float)sx;
                 if (pa == 1) v = cscale(v, kx);
@@ -434,7 +428,8 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
             for (int i = 0; i < E; ++i) o[(p + P * i) * estride] = y[i];
         }
     };
-    auto is_delta = [&](int f) { return ((args.codes[f] >> 8) & 3) == XS_DELTA; };
+    auto src_of = [&](int f) { return (args.codes[f] >> 8) & 3; };
+    auto is_delta = [&](int f) { return src_of(f) == XS_DELTA; };
     // transform and store outputs f (and f + 1 when paired) from column sc
     auto emit = [&](int f, bool pair, const float2 (&sc)[E]) {
         if (PAIR && pair) {
@@ -460,15 +455,30 @@ __device__ __forceinline__ void xexp_body(const XExpArgs& args, const float2* __
     if (f < args.nout) {
         float2 xs[E];
         load_col(two ? args.src1 : args.src0, xs);
+        bool phi = false;                                 // xs holds theta / k^2
         while (f < args.nout) {
-            if (is_delta(f)) {                            // a later delta output: re-read delta
+            const int src = src_of(f);
+            if (src == XS_DELTA) {                        // a later delta output: re-read delta
                 float2 d[E];
                 load_col(args.src0, d);
                 emit(f, false, d);
                 f += 1;
                 continue;
             }
-            const bool pair = PAIR && f + 1 < args.nout && !is_delta(f + 1);
+            if (src == XS_PHI && !phi) {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int sx = signed_idx(p + P * i, N);
+                    const int s2 = sx * sx + syz;
+                    const float g = s2 ? inv_kF2 / (float)s2 : 0.f;   // 1 / k^2, 0 at k = 0
+                    xs[i] = cscale(xs[i], g);
+                }
+                phi = true;
+            } else if (src == XS_THETA && phi) {          // theta after phi: re-read theta
+                load_col(two ? args.src1 : args.src0, xs);
+                phi = false;
+            }
+            const bool pair = PAIR && f + 1 < args.nout && src_of(f + 1) == src;
             emit(f, pair, xs);
             f += pair ? 2 : 1;
         }
@@ -839,11 +849,9 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     const float2 gv = pr[p + P * i];
-                    const float2 fg = make_float2(x[i].x * gv.x, x[i].y * gv.y);
-                    accA[t][i].x = fmaf(ca, fg.x, accA[t][i].x);
-                    accA[t][i].y = fmaf(ca, fg.y, accA[t][i].y);
-                    accB[t][i].x = fmaf(cb, fg.x, accB[t][i].x);
-                    accB[t][i].y = fmaf(cb, fg.y, accB[t][i].y);
+                    const float2 fg = lmul(x[i], gv);
+                    accA[t][i] = lfma(ca, fg, accA[t][i]);
+                    accB[t][i] = lfma(cb, fg, accB[t][i]);
                 }
             }
         }
@@ -877,8 +885,7 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
             float2* colx = tex + c * PITCH;
 #pragma unroll
             for (int i = 0; i < E; ++i)
-                colx[p + P * i] = make_float2(fmaf(c0, accA[t][i].x, c1 * accB[t][i].x),
-                                              fmaf(c0, accA[t][i].y, c1 * accB[t][i].y));
+                colx[p + P * i] = lfma(c0, accA[t][i], cscale(accB[t][i], c1));
             __syncthreads();
             tile_store<M, TZ, PITCH, NTH>(reinterpret_cast<float2*>(h ? T.out_b : T.out_a), tex, row0, rows);
         }
@@ -1082,11 +1089,9 @@ __device__ __forceinline__ void zrow_body(const ZPairArgs& args, const float2* _
 #pragma unroll
                         for (int i = 0; i < E; ++i) {
                             const float2 gv = pr[p + P * i];
-                            const float2 fg = make_float2(x[i].x * gv.x, x[i].y * gv.y);
-                            accA[t][i].x = fmaf(ca, fg.x, accA[t][i].x);
-                            accA[t][i].y = fmaf(ca, fg.y, accA[t][i].y);
-                            accB[t][i].x = fmaf(cb, fg.x, accB[t][i].x);
-                            accB[t][i].y = fmaf(cb, fg.y, accB[t][i].y);
+                            const float2 fg = lmul(x[i], gv);
+                            accA[t][i] = lfma(ca, fg, accA[t][i]);
+                            accB[t][i] = lfma(cb, fg, accB[t][i]);
                         }
                     }
                 }
@@ -1103,20 +1108,16 @@ __device__ __forceinline__ void zrow_body(const ZPairArgs& args, const float2* _
 #pragma unroll
                     for (int i = 0; i < E; ++i) {
                         const float2 va = ia[p + P * i], vb = ib[p + P * i];
-                        accA[t][i].x += va.x;
-                        accA[t][i].y += va.y;
-                        accB[t][i].x += vb.x;
-                        accB[t][i].y += vb.y;
+                        accA[t][i] = cadd(accA[t][i], va);
+                        accB[t][i] = cadd(accB[t][i], vb);
                     }
                 }
                 float2* oa = reinterpret_cast<float2*>(T.out_a) + row * M;
                 float2* ob = reinterpret_cast<float2*>(T.out_b) + row * M;
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
-                    oa[p + P * i] = make_float2(fmaf(T.ca0, accA[t][i].x, T.ca1 * accB[t][i].x),
-                                                fmaf(T.ca0, accA[t][i].y, T.ca1 * accB[t][i].y));
-                    ob[p + P * i] = make_float2(fmaf(T.cb0, accA[t][i].x, T.cb1 * accB[t][i].x),
-                                                fmaf(T.cb0, accA[t][i].y, T.cb1 * accB[t][i].y));
+                    oa[p + P * i] = lfma(T.ca0, accA[t][i], cscale(accB[t][i], T.ca1));
+                    ob[p + P * i] = lfma(T.cb0, accA[t][i], cscale(accB[t][i], T.cb1));
                 }
             }
         }
