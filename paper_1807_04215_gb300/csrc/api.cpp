@@ -854,8 +854,9 @@ gridspt_status run_orders_div(const gridspt_plan_s* p, float2* d1, const std::fu
             pa.out = reinterpret_cast<float*>(src);
             pa.scale = (float)(1.0 / (double)cells);
             CKP(PK_PRODUCT, fb * 4.0 * m, s, launch_product_div(p->geo, pa, s), "divergence-form sources");
-            CKP(PK_ZR2C, 8 * fb, s, launch_zr2c(p->geo, src, src, F, 4, 1.0f, s), "z r2c (divergence form)");
-            CKP(PK_Y_FWD, 8 * fb, s, launch_colpass_fwd(p->geo, src, F, 4, 1, 0, -1, s), "y pass fwd (divergence form)");
+            CKP(PK_ZR2C, 8 * fb, s, launch_zr2c(p->geo, src, src, F, 4, 1.0f, 0, s), "z r2c (divergence form)");
+            CKP(PK_Y_FWD, 8 * fb, s, launch_colpass_fwd(p->geo, src, F, 4, 1, 0, -1, 0, s),
+                "y pass fwd (divergence form)");
         } else if (m == n_max) {
             break;
         }
@@ -910,11 +911,23 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
                     q.zero_k0 = 1;
                     return q;
                 };
-                CKQ(PK_ZR2C, 4 * fb, s, launch_zr2c(p->geo, dk, dk, F, 2, 1.0f, s), "z r2c", col(Q_ZR2C));
-                CKQ(PK_Y_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 1, 0, -1, s), "y pass fwd",
-                    col(Q_COLY));
+                // A band-limited order below n_max: its x pass reads only the band
+                // columns (|ky|, kz < band) and its spectra are zeroed outside them
+                // after it, so the z pass writes only kz < band and the y pass
+                // transforms only those columns and writes only their band rows.
+                int fband = 0;
+                if (m < n_max) {
+                    const int b = order_band(p, m, start_order);
+                    if (b > 0 && b + (b & 1) < p->geo.M) fband = b + (b & 1);
+                }
+                const double fo = fband ? (double)fband / p->geo.M : 1.0;
+                const double fr = fband ? (2.0 * fband - 1.0) / p->geo.N : 1.0;
+                CKQ(PK_ZR2C, (2 + 2 * fo) * fb, s, launch_zr2c(p->geo, dk, dk, F, 2, 1.0f, fband, s), "z r2c",
+                    col(Q_ZR2C));
+                CKQ(PK_Y_FWD, 2 * fo * (1 + fr) * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 1, 0, -1, fband, s),
+                    "y pass fwd", col(Q_COLY));
                 if (m == n_max) {
-                    CKQ(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 2, order_cut(p, m), s),
+                    CKQ(PK_X_FWD, 4 * fb, s, launch_colpass_fwd(p->geo, dk, F, 2, 0, 2, order_cut(p, m), 0, s),
                         "x pass fwd", col(Q_COLX));
                     break;
                 }
@@ -1266,29 +1279,48 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
         cudaEventDestroy(a);
         return cuda_fail(e, "event");
     }
-    // per pass, the launch of an order >= 2 expansion (x: 2 spectra -> 7, y: 7 -> 12,
-    // z: 12 -> 17) or of the forward passes of delta_n, theta_n, on scratch fields
+    // per pass, on scratch fields: the x and y expansions of orders 1 .. n_max - 1
+    // as a run from delta_1 launches them (order 1 and the band-limited orders
+    // move only their band columns, so the timing weighs the variants as the
+    // run does); the z expansion of an order >= 2 (12 -> 17, store-only and
+    // fused with pair products); the forward passes of delta_n, theta_n
     auto run = [&](const Geo& g, int pass) -> cudaError_t {
         XExpArgs xa{};
         YZExpArgs ya{}, za{};
         expansion_codes(2, xa, ya, za);
         switch (pass) {
-            case TV_COLPASS: return launch_colpass_fwd(g, f0, F, 2, 1, 0, -1, s);
-            case TV_XEXP:   // forward first, as every x pass of orders >= 2
-                xa.src0 = f0;
-                xa.src1 = f0 + F;
-                xa.out = f0 + 2 * F;
-                xa.out_stride = F;
-                xa.s2_nl = -1;
-                xa.fwd_first = 1;
-                xa.zero_k0 = 1;
-                return launch_xexp(g, xa, s);
-            case TV_YEXP:
-                ya.in = f0;
-                ya.in_stride = F;
-                ya.out = f0 + 7 * F;
-                ya.out_stride = F;
-                return launch_yexp(g, ya, s);
+            case TV_COLPASS: return launch_colpass_fwd(g, f0, F, 2, 1, 0, -1, 0, s);
+            case TV_XEXP:
+            case TV_YEXP: {
+                const int top = p->d.n_max > 2 ? p->d.n_max - 1 : 1;
+                for (int m = 1; m <= top; ++m) {
+                    XExpArgs xm{};
+                    YZExpArgs ym{}, zm{};
+                    expansion_codes(m, xm, ym, zm);
+                    double fx = 1.0, fyi = 1.0, fyo = 1.0;
+                    if (m == 1) order1_band(p, xm, ym, zm, &fx, &fyi, &fyo);
+                    else if (const int band = order_band(p, m, 2)) set_band(p, band, xm, ym, zm, &fx, &fyi, &fyo);
+                    cudaError_t em;
+                    if (pass == TV_XEXP) {   // order 1 backward only, orders >= 2 forward first
+                        xm.src0 = f0;
+                        xm.src1 = m == 1 ? f0 : f0 + F;
+                        xm.out = f0 + 2 * F;
+                        xm.out_stride = F;
+                        xm.s2_nl = m == 1 ? -1 : order_cut(p, m);
+                        xm.fwd_first = m >= 2;
+                        xm.zero_k0 = m >= 2;
+                        em = launch_xexp(g, xm, s);
+                    } else {
+                        ym.in = f0;
+                        ym.in_stride = F;
+                        ym.out = f0 + 7 * F;
+                        ym.out_stride = F;
+                        em = launch_yexp(g, ym, s);
+                    }
+                    if (em != cudaSuccess) return em;
+                }
+                return cudaSuccess;
+            }
             case TV_ZEXP: {
                 za.in = f0;
                 za.in_stride = F;
@@ -1314,7 +1346,7 @@ gridspt_status gridspt_autotune(gridspt_plan p, void* scratch, size_t scratch_by
                 T.ca1 = T.cb0 = 0.f;
                 return launch_zexp_pairs(g, pa, s);
             }
-            default: return launch_zr2c(g, f0, f0, F, 2, 1.0f, s);
+            default: return launch_zr2c(g, f0, f0, F, 2, 1.0f, 0, s);
         }
     };
     int best[TV_COUNT];
@@ -1482,9 +1514,9 @@ gridspt_status gridspt_r2c(gridspt_plan p, const float* in_x, void* out_k, int32
     const long long F = field_c(p);
     float2* o = static_cast<float2*>(out_k);
     const float scale = (float)(1.0 / (double)field_floats(p));
-    CK(launch_zr2c(p->geo, reinterpret_cast<const float2*>(in_x), o, F, count, scale, s), "z r2c");
-    CK(launch_colpass_fwd(p->geo, o, F, count, 1, 0, -1, s), "y pass");
-    CK(launch_colpass_fwd(p->geo, o, F, count, 0, 1, -1, s), "x pass");
+    CK(launch_zr2c(p->geo, reinterpret_cast<const float2*>(in_x), o, F, count, scale, 0, s), "z r2c");
+    CK(launch_colpass_fwd(p->geo, o, F, count, 1, 0, -1, 0, s), "y pass");
+    CK(launch_colpass_fwd(p->geo, o, F, count, 0, 1, -1, 0, s), "x pass");
     return GRIDSPT_OK;
 }
 

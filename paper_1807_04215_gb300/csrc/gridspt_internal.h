@@ -195,11 +195,14 @@ cudaError_t launch_zexp(const Geo& g, const YZExpArgs& a, cudaStream_t s);
 // Forward column transform along x (axis 0) or y (axis 1) of `count` fields,
 // in place. finalize (x axis): 1 zeroes the Nyquist modes and |s|^2 > s2_nl
 // (s2_nl < 0: no cut); 2 also the k = 0 mode (orders n >= 2 of the recursion).
+// band > 0 (y axis, 0 < band < N/2): only the columns kz < band are
+// transformed and only their rows |ky| < band written; the rest is left as is.
 cudaError_t launch_colpass_fwd(const Geo& g, float2* data, long long fstride, int count, int axis,
-                               int finalize, long long s2_nl, cudaStream_t s);
-// Contiguous-axis real-to-complex with output scale.
+                               int finalize, long long s2_nl, int band, cudaStream_t s);
+// Contiguous-axis real-to-complex with output scale; band > 0 (< N/2): only
+// the coefficients kz < band are written.
 cudaError_t launch_zr2c(const Geo& g, const float2* in, float2* out, long long fstride, int count,
-                        float scale, cudaStream_t s);
+                        float scale, int band, cudaStream_t s);
 cudaError_t launch_product(const Geo& g, const ProductArgs& a, cudaStream_t s);
 
 // Divergence-form sources of order n: V_n = sum_m delta_m u_{n-m} (3 fields) and

@@ -259,8 +259,9 @@ __device__ void q_tile(const QStage& st, long long tile, float2* sm, bool tr) {
         case Q_XEXP0: xexp_body<N, TZ, 0>(st.x, st.tw, st.kF, st.inv_kF2, bx, by, sm, tr); break;
         case Q_XEXP1: xexp_body<N, TZ, 1>(st.x, st.tw, st.kF, st.inv_kF2, bx, by, sm, tr); break;
         case Q_YEXP: yexp_body<N, TZ, false>(st.y, st.tw, st.kF, bx, by, sm, tr); break;
-        case Q_COLY: colpass_body<N, TZ, 1, false>(st.data, st.fstride, st.tw, -1, 0, bx, by, bz, sm, tr); break;
-        case Q_COLX: colpass_body<N, TZ, 0, true>(st.data, st.fstride, st.tw, st.s2, st.zero_k0, bx, by, bz, sm, tr);
+        case Q_COLY: colpass_body<N, TZ, 1, false>(st.data, st.fstride, st.tw, -1, 0, 0, bx, by, bz, sm, tr); break;
+        case Q_COLX:
+            colpass_body<N, TZ, 0, true>(st.data, st.fstride, st.tw, st.s2, st.zero_k0, 0, bx, by, bz, sm, tr);
             break;
         case Q_ZR2C: q_zr2c<N>(st, tile, sm, tr); break;
         case Q_Z: {

@@ -103,6 +103,8 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_by
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Hint: bring the 128-byte line of p into L2 (no registers, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Issue (without waiting) the copy of TZ rows of M float2 into a shared tile.
@@ -172,10 +174,14 @@ __device__ __forceinline__ void tile_store(float2* dst, const float2* tile, long
 // the twiddle table already sits at the start of sm (a previous tile of the
 // same size and table layout in the same block loaded it, and every thread
 // has passed a block barrier since).
+// band > 0 (y axis): only the columns kz < band are transformed, and only the
+// rows |ky| < band of them are written (a band-limited order, whose x pass
+// reads only those and whose spectra are zeroed outside them afterwards).
 template <int N, int TZ, int AXIS, bool FIN>
 __device__ __forceinline__ void colpass_body(float2* __restrict__ data, long long fstride,
                                              const float2* __restrict__ twg, long long s2_nl, int zero_k0,
-                                             int bx, int by, int bz, float2* sm, bool table_ready = false) {
+                                             int band, int bx, int by, int bz, float2* sm,
+                                             bool table_ready = false) {
     constexpr int M = N / 2, E = fft_elems(N), P = N / E;
     float2* tw = sm;
     float2* buf = sm + N;
@@ -183,7 +189,7 @@ __device__ __forceinline__ void colpass_body(float2* __restrict__ data, long lon
     if (!table_ready) load_table(tw, twg, N);
     const int kz = bx * TZ + c;
     const int a = by;
-    const bool act = kz < M;
+    const bool act = kz < M && (band <= 0 || kz < band);
     constexpr long long estride = AXIS == 0 ? (long long)N * M : (long long)M;
     constexpr long long astride = AXIS == 0 ? (long long)M : (long long)N * M;
     float2* col = data + bz * fstride + a * astride + kz;
@@ -205,22 +211,26 @@ __device__ __forceinline__ void colpass_body(float2* __restrict__ data, long lon
     }
     if (act) {
 #pragma unroll
-        for (int i = 0; i < E; ++i) col[(p + P * i) * estride] = x[i];
+        for (int i = 0; i < E; ++i) {
+            const int n = p + P * i;
+            if (band <= 0 || n < band || n > N - band) col[(p + P * i) * estride] = x[i];
+        }
     }
 }
 
 template <int N, int TZ, int AXIS, bool FIN>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PC)
 k_colpass(float2* __restrict__ data, long long fstride, const float2* __restrict__ twg,
-          long long s2_nl, int zero_k0) {
+          long long s2_nl, int zero_k0, int band) {
     extern __shared__ float2 sm[];
-    colpass_body<N, TZ, AXIS, FIN>(data, fstride, twg, s2_nl, zero_k0, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+    colpass_body<N, TZ, AXIS, FIN>(data, fstride, twg, s2_nl, zero_k0, band, blockIdx.x, blockIdx.y, blockIdx.z,
+                                   sm);
 }
 
 // ------------------------------------------------ contiguous axis: R2C
 template <int N, int TZ>
 __global__ void __launch_bounds__(TZ * Cfg<N>::PZ)
-k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restrict__ twg, float scale) {
+k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restrict__ twg, float scale, int band) {
     constexpr int M = N / 2, E = fft_elems(M), P = M / E, PITCH = Cfg<N>::PITCH;
     extern __shared__ float2 sm[];
     float2* tw = sm;
@@ -249,7 +259,7 @@ k_zr2c(const float2* in, float2* out, long long fstride, const float2* __restric
         const int idx = tid + u * NTHR;
         const int r = idx / M, k = idx - r * M;
         const long long row = row0 + r;
-        if (idx >= NV || row >= rows) continue;
+        if (idx >= NV || row >= rows || (band > 0 && k >= band)) continue;
         const float2 Z = tile[r * PITCH + k];
         const float2 Zr = cconj(tile[r * PITCH + (k ? M - k : 0)]);
         const float2 S = cadd(Z, Zr);                      // 2 E[k]
@@ -500,7 +510,8 @@ k_xexp(const __grid_constant__ XExpArgs args, const float2* __restrict__ twg, fl
 //
 // PF: the next input's column tile is copied into a second shared buffer by
 // cp.async (8-byte, zero-filled where the band excludes it) while the outputs
-// of the current input are transformed.
+// of the current input are transformed. Otherwise the next input's column is
+// prefetched into L2 (prefetch.global.L2), so its loads wait for L2, not HBM.
 // PAIR: two consecutive outputs of the same input are transformed together by
 // fft_column_pair (as in xexp_body; bit for bit the same outputs).
 template <int N, int TZ, bool PF, bool PAIR = false>
@@ -544,6 +555,19 @@ __device__ __forceinline__ void yexp_body(const YZExpArgs& args, const float2* _
             }
             cur = in;
             have_next = false;
+            if constexpr (!PF) {                 // the next distinct input: prefetched into L2 meanwhile
+                int g2 = f + 1;
+                while (g2 < args.nout && (args.codes[g2] & 255) == in) ++g2;
+                if (g2 < args.nout) {
+                    const float2* col = args.in + (args.codes[g2] & 255) * args.in_stride + colofs;
+#pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        const int sy = signed_idx(p + P * i, N);
+                        const bool live = act && (B <= 0 || (sy < B && -sy < B));
+                        if (live) prefetch_l2(col + (p + P * i) * estride);
+                    }
+                }
+            }
             if constexpr (PF) {                  // the next distinct input, if any
                 int g2 = f + 1;
                 while (g2 < args.nout && (args.codes[g2] & 255) == in) ++g2;
@@ -1464,7 +1488,7 @@ k_zrow_shell(const float2* __restrict__ in, long long in_stride, int band, const
 template <int N>
 __global__ void __launch_bounds__(kRowWarps * 32, 3)
 k_zrow_r2c(const float2* in, float2* out, long long fstride, int count, const float2* __restrict__ twg,
-           float scale) {
+           float scale, int band) {
     using C = RowCfg<N>;
     constexpr int M = C::M, E = C::E, P = C::P, RW = C::RW;
     static_assert(C::ok, "warp-row z pass needs P <= 32, 32 % P == 0 and a power-of-two row");
@@ -1497,7 +1521,7 @@ k_zrow_r2c(const float2* in, float2* out, long long fstride, int count, const fl
             const float2 Zr = cconj(xrow[xpad(k ? M - k : 0)]);
             const float2 S = cadd(Z, Zr);                            // 2 E[k]
             const float2 t = cmul(cconj(twp[i * P + p]), csub(Z, Zr));  // e^{-2 pi i k/N} 2i O[k]
-            dst[k] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
+            if (band <= 0 || k < band) dst[k] = make_float2(half * (S.x + t.y), half * (S.y - t.x));
         }
         __syncwarp();                                    // exchange buffer free for the next row
     }
@@ -1520,14 +1544,15 @@ struct Launch {
     static constexpr int M = N / 2;
     static constexpr int PC = Cfg<N>::PC, PZ = Cfg<N>::PZ, PITCH = Cfg<N>::PITCH;
     static cudaError_t colpass(const Geo& g, float2* d, long long fs, int count, int axis, int fin,
-                               long long s2_nl, cudaStream_t s) {
-        dim3 grid((M + TZC - 1) / TZC, N, count);
+                               long long s2_nl, int band, cudaStream_t s) {
+        const int B = axis == 1 && band > 0 && band < M ? band : 0;
+        dim3 grid(((B ? B : M) + TZC - 1) / TZC, N, count);
         const size_t smem = colpass_smem<N, TZC>();
         cudaError_t e;
 #define GRIDSPT_COL(AX_, FIN_)                                                        \
     e = set_smem(k_colpass<N, TZC, AX_, FIN_>, smem);                                 \
     if (e != cudaSuccess) return e;                                                   \
-    k_colpass<N, TZC, AX_, FIN_><<<grid, TZC * PC, smem, s>>>(d, fs, g.tw, s2_nl, fin == 2); \
+    k_colpass<N, TZC, AX_, FIN_><<<grid, TZC * PC, smem, s>>>(d, fs, g.tw, s2_nl, fin == 2, B); \
     return cudaGetLastError();
         if (axis == 0) {
             if (fin) { GRIDSPT_COL(0, true) }
@@ -1537,7 +1562,7 @@ struct Launch {
 #undef GRIDSPT_COL
     }
     static cudaError_t zrow_r2c(const Geo& g, const float2* in, float2* out, long long fs, int count, float scale,
-                                cudaStream_t s) {
+                                int band, cudaStream_t s) {
         using C = RowCfg<N>;
         if constexpr (!C::ok) {
             return cudaErrorNotSupported;
@@ -1555,18 +1580,18 @@ struct Launch {
             const long long need = (groups + kRowWarps - 1) / kRowWarps;
             const long long resident = (long long)(per > 0 ? per : 1) * sms;
             k_zrow_r2c<N><<<(unsigned)(need < resident ? need : resident), kRowWarps * 32, smem, s>>>(
-                in, out, fs, count, g.tw, scale);
+                in, out, fs, count, g.tw, scale, band > 0 && band < M ? band : 0);
             return cudaGetLastError();
         }
     }
     static cudaError_t zr2c(const Geo& g, const float2* in, float2* out, long long fs, int count,
-                            float scale, cudaStream_t s) {
+                            float scale, int band, cudaStream_t s) {
         const long long rows = (long long)N * N;
         dim3 grid((unsigned)((rows + TZZ - 1) / TZZ), count);
         const size_t smem = sizeof(float2) * (N + (size_t)TZZ * PITCH);
         cudaError_t e = set_smem(k_zr2c<N, TZZ>, smem);
         if (e != cudaSuccess) return e;
-        k_zr2c<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(in, out, fs, g.tw, scale);
+        k_zr2c<N, TZZ><<<grid, TZZ * PZ, smem, s>>>(in, out, fs, g.tw, scale, band > 0 && band < M ? band : 0);
         return cudaGetLastError();
     }
     template <bool PAIR = false>
@@ -1754,16 +1779,16 @@ struct Launch {
 // variant v selects tile widths: v = 0 default, v = 1 alternative.
 #define GRIDSPT_TRANSFORM_SIZE(N)                                                                          \
     cudaError_t transform_colpass_##N(const Geo& g, float2* d, long long fs, int count, int axis, int fin, \
-                                      long long s2, int v, cudaStream_t s) {                               \
-        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::colpass(g, d, fs, count, axis, fin, s2, s)       \
-                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::colpass(g, d, fs, count, axis, fin, s2, s);      \
+                                      long long s2, int band, int v, cudaStream_t s) {                     \
+        return v ? Launch<N, Cfg<N>::TZC1, Cfg<N>::TZZ0>::colpass(g, d, fs, count, axis, fin, s2, band, s) \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::colpass(g, d, fs, count, axis, fin, s2, band, s); \
     }                                                                                                      \
     cudaError_t transform_zr2c_##N(const Geo& g, const float2* in, float2* out, long long fs, int count,   \
-                                   float scale, int v, cudaStream_t s) {                                   \
+                                   float scale, int band, int v, cudaStream_t s) {                         \
         if (v == 2 && RowCfg<N>::ok)                                                                       \
-            return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zrow_r2c(g, in, out, fs, count, scale, s);        \
-        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ1>::zr2c(g, in, out, fs, count, scale, s)            \
-                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zr2c(g, in, out, fs, count, scale, s);           \
+            return Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zrow_r2c(g, in, out, fs, count, scale, band, s);  \
+        return v ? Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ1>::zr2c(g, in, out, fs, count, scale, band, s)      \
+                 : Launch<N, Cfg<N>::TZC0, Cfg<N>::TZZ0>::zr2c(g, in, out, fs, count, scale, band, s);     \
     }                                                                                                      \
     cudaError_t transform_xexp_##N(const Geo& g, const XExpArgs& a, int v, cudaStream_t s) {               \
         if (a.fwd_first && a.div_in) /* four input columns in registers: the narrower tile */              \

@@ -8,9 +8,9 @@ namespace gridspt {
     X(512) X(768) X(1024)
 
 #define GRIDSPT_DECLARE(N)                                                                                 \
-    cudaError_t transform_colpass_##N(const Geo&, float2*, long long, int, int, int, long long, int,       \
+    cudaError_t transform_colpass_##N(const Geo&, float2*, long long, int, int, int, long long, int, int,  \
                                       cudaStream_t);                                                       \
-    cudaError_t transform_zr2c_##N(const Geo&, const float2*, float2*, long long, int, float, int,         \
+    cudaError_t transform_zr2c_##N(const Geo&, const float2*, float2*, long long, int, float, int, int,    \
                                    cudaStream_t);                                                          \
     cudaError_t transform_xexp_##N(const Geo&, const XExpArgs&, int, cudaStream_t);                        \
     cudaError_t transform_yexp_##N(const Geo&, const YZExpArgs&, int, cudaStream_t);                       \
@@ -32,10 +32,11 @@ bool supported_n(int N) {
 }
 
 cudaError_t launch_colpass_fwd(const Geo& g, float2* data, long long fstride, int count, int axis,
-                               int finalize, long long s2_nl, cudaStream_t s) {
+                               int finalize, long long s2_nl, int band, cudaStream_t s) {
     switch (g.N) {
-#define GRIDSPT_CASE(n) \
-    case n: return transform_colpass_##n(g, data, fstride, count, axis, finalize, s2_nl, g.var[TV_COLPASS], s);
+#define GRIDSPT_CASE(n)                                                                                       \
+    case n:                                                                                                   \
+        return transform_colpass_##n(g, data, fstride, count, axis, finalize, s2_nl, band, g.var[TV_COLPASS], s);
         GRIDSPT_ALL_N(GRIDSPT_CASE)
 #undef GRIDSPT_CASE
         default: return cudaErrorInvalidValue;
@@ -43,9 +44,10 @@ cudaError_t launch_colpass_fwd(const Geo& g, float2* data, long long fstride, in
 }
 
 cudaError_t launch_zr2c(const Geo& g, const float2* in, float2* out, long long fstride, int count, float scale,
-                        cudaStream_t s) {
+                        int band, cudaStream_t s) {
     switch (g.N) {
-#define GRIDSPT_CASE(n) case n: return transform_zr2c_##n(g, in, out, fstride, count, scale, g.var[TV_ZR2C], s);
+#define GRIDSPT_CASE(n) \
+    case n: return transform_zr2c_##n(g, in, out, fstride, count, scale, band, g.var[TV_ZR2C], s);
         GRIDSPT_ALL_N(GRIDSPT_CASE)
 #undef GRIDSPT_CASE
         default: return cudaErrorInvalidValue;
