@@ -519,6 +519,31 @@ void pair_table(int j, PairTarget& T) {
     }
 }
 
+// The diagonal pair (1, 1) of order 2 (Eq. recursion_formula with m = n - m =
+// 1) as a target of order 1's own z pass: every product of two order-1 fields
+// is added when the later of the two is formed (the earlier one is read back
+// from the rows this launch has just stored; a square uses the formed field
+// itself, pfield -1). Order-1 stored fields: 0 delta (= theta), 1..3 grad delta
+// (= grad theta), 4..6 u, 7..9 d_a u_a, 10..12 the off-diagonal d_a u_b.
+// A = delta theta + grad delta . u, B = u . grad theta + sum_ab (d_a u_b)^2.
+void diag1_table(const YZExpArgs& za, PairTarget& T) {
+    int pos[17];
+    for (int sl = 0; sl < 17; ++sl) pos[sl] = -1;
+    for (int f = 0; f < za.nout; ++f) pos[za.codes[f] >> 16] = f;
+    for (int sl = 0; sl < 17; ++sl) T.pcount[sl] = 0;
+    auto term = [&](int a, int b, float ca, float cb) {
+        const int late = pos[a] >= pos[b] ? a : b, early = late == a ? b : a;
+        const int q = T.pcount[late]++;
+        T.pfield[late][q] = a == b ? -1 : early;
+        T.pcoef_a[late][q] = ca;
+        T.pcoef_b[late][q] = cb;
+    };
+    term(0, 0, 1.f, 0.f);                                   // delta_1 theta_1
+    for (int a = 0; a < 3; ++a) term(1 + a, 4 + a, 1.f, 1.f);  // grad delta . u and u . grad theta
+    for (int t = 0; t < 3; ++t) term(7 + t, 7 + t, 0.f, 1.f);  // (d_a u_a)^2
+    for (int t = 0; t < 3; ++t) term(10 + t, 10 + t, 0.f, 2.f);  // 2 (d_a u_b)^2, a < b
+}
+
 // z pass of order m fused with the pair products (m, j), j < m, m + j <= n_max,
 // for the targets n' = m + j >= start. Stores the order's real fields when a
 // later order needs them (2m <= n_max). More than two targets are split over
@@ -545,6 +570,16 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
         // fields per output over all its targets (order 1 supplies at most one
         // partner per output, higher orders two)
         int partners = 0;
+        if (m == 1 && n_max >= 2 && start <= 2 && a.store) {   // the diagonal pair (1, 1): all of order 2
+            PairTarget& T = a.t[a.ntargets++];
+            T.partner = a.store;
+            diag1_table(za, T);
+            T.out_a = reinterpret_cast<float*>(spec_delta[2]);
+            T.out_b = reinterpret_cast<float*>(spec_delta[2] + field_c(p));
+            recursion_coefs(p, 2, &T.ca0, &T.ca1, &T.cb0, &T.cb1);
+            partners = 1;
+            bytes += fb * 2;   // delta_2, theta_2 written; the partners are this launch's own stores
+        }
         for (size_t q = first; q < js.size() && a.ntargets < kMaxPairTargets; ++q, ++first) {
             const int j = js[q], n = m + j;
             if (partners + (j == 1 ? 1 : 2) > kMaxPartners) break;
@@ -576,7 +611,8 @@ gridspt_status zexp_pairs(const gridspt_plan_s* p, int m, const YZExpArgs& za, f
         }
         for (int sl = 0; sl < 17; ++sl) {   // the kernels stage at most kMaxPartners partner tiles
             int c = 0;
-            for (int t = 0; t < a.ntargets; ++t) c += a.t[t].pcount[sl];
+            for (int t = 0; t < a.ntargets; ++t)
+                for (int q = 0; q < a.t[t].pcount[sl]; ++q) c += a.t[t].pfield[sl][q] >= 0 ? 1 : 0;
             if (c > kMaxPartners) return fail(GRIDSPT_E_INVALID, "internal: %d partner fields for one output", c);
         }
         if (!a.store && a.ntargets == 0) break;
@@ -934,7 +970,8 @@ gridspt_status run_orders_impl(gridspt_plan p, const void* delta1_k, int32_t sta
             }
             if (m == n_max) break;
             if (gridspt_status st = derive_order(p, m, dk, tk, w, !given, start_order, spec_delta, s)) return st;
-            if (2 * m <= n_max && 2 * m >= start_order) {   // diagonal pair (m, m) of order 2m
+            if (m >= 2 && 2 * m <= n_max && 2 * m >= start_order) {   // diagonal pair (m, m) of order 2m
+                // ((1, 1) is a target of order 1's z pass)
                 ProductArgs pa{};
                 pa.ws = w;
                 pa.cells = field_floats(p);

@@ -153,7 +153,8 @@ struct PairTarget {
     float* out_b;
     float ca0, ca1, cb0, cb1;
     int pcount[17];             // per produced slot: number of partner fields (0..2)
-    int pfield[17][2];          // partner field index in the stored order
+    int pfield[17][2];          // partner field index in the stored order; -1: the produced field
+                                // itself (a square), no partner rows are read
     float pcoef_a[17][2];       // contribution coefficients to A and B
     float pcoef_b[17][2];
 };

@@ -163,11 +163,12 @@ __device__ void q_zrow(const ZPairArgs& args, const float2* __restrict__ twg, fl
                 const PairTarget& T = args.t[t];
                 for (int q = 0; q < T.pcount[slot]; ++q) {
                     const float ca = T.pcoef_a[slot][q], cb = T.pcoef_b[slot][q];
+                    const bool sq = T.pfield[slot][q] < 0;                    // a square
                     const float2* pr = reinterpret_cast<const float2*>(T.partner) +
-                                       (long long)T.pfield[slot][q] * fstride2 + row * M;
+                                       (long long)(sq ? 0 : T.pfield[slot][q]) * fstride2 + row * M;
 #pragma unroll
                     for (int i = 0; i < E; ++i) {
-                        const float2 gv = pr[p + P * i];
+                        const float2 gv = sq ? x[i] : pr[p + P * i];
                         const float2 fg = lmul(x[i], gv);
                         accA[t][i] = lfma(ca, fg, accA[t][i]);
                         accB[t][i] = lfma(cb, fg, accB[t][i]);

@@ -818,10 +818,13 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
         for (int t = 0; t < NT; ++t) {
             if (t >= args.ntargets) break;
             const PairTarget& T = args.t[t];
-            for (int q = 0; q < T.pcount[slot]; ++q, ++np)
+            for (int q = 0; q < T.pcount[slot]; ++q) {
+                if (T.pfield[slot][q] < 0) continue;                // a square: no partner tile
                 tile_prefetch<M, TZ, PITCH, NTH>(tpt + np * TZ * PITCH, reinterpret_cast<const float2*>(T.partner) +
                                                                          (long long)T.pfield[slot][q] * fstride2,
                                                  row0, rows);
+                ++np;
+            }
         }
         if (in != cur) {
             tile_load<M, TZ, PITCH, NTH>(tin, z.in + in * z.in_stride, row0, rows, z.band);
@@ -867,12 +870,14 @@ k_zexp_pairs(ZPairArgs args, const float2* __restrict__ twg, float kF) {
         for (int t = 0; t < NT; ++t) {
             if (t >= args.ntargets) break;
             const PairTarget& T = args.t[t];
-            for (int q = 0; q < T.pcount[slot]; ++q, ++np) {
+            for (int q = 0; q < T.pcount[slot]; ++q) {
                 const float ca = T.pcoef_a[slot][q], cb = T.pcoef_b[slot][q];
+                const bool sq = T.pfield[slot][q] < 0;
                 const float2* pr = tpt + np * TZ * PITCH + c * PITCH;
+                if (!sq) ++np;
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
-                    const float2 gv = pr[p + P * i];
+                    const float2 gv = sq ? x[i] : pr[p + P * i];
                     const float2 fg = lmul(x[i], gv);
                     accA[t][i] = lfma(ca, fg, accA[t][i]);
                     accB[t][i] = lfma(cb, fg, accB[t][i]);
@@ -1029,12 +1034,14 @@ __device__ __forceinline__ void zrow_body(const ZPairArgs& args, const float2* _
                 for (int t = 0; t < NT; ++t) {
                     if (t >= args.ntargets) break;
                     const PairTarget& T = args.t[t];
-                    for (int q = 0; q < T.pcount[slot]; ++q, ++np) {
+                    for (int q = 0; q < T.pcount[slot]; ++q) {
+                        if (T.pfield[slot][q] < 0) continue;            // a square: no partner rows
                         const float2* src = reinterpret_cast<const float2*>(T.partner) +
                                             (long long)T.pfield[slot][q] * fstride2 + row0 * M;
 #pragma unroll
                         for (int u = 0; u < WIN / 64; ++u)
                             cp_async16(wpt + np * WIN + 2 * (lane + 32 * u), src + 2 * (lane + 32 * u));
+                        ++np;
                     }
                 }
             }
@@ -1107,16 +1114,18 @@ __device__ __forceinline__ void zrow_body(const ZPairArgs& args, const float2* _
                 for (int t = 0; t < NT; ++t) {
                     if (t >= args.ntargets) break;
                     const PairTarget& T = args.t[t];
-                    for (int q = 0; q < T.pcount[slot]; ++q, ++np) {
+                    for (int q = 0; q < T.pcount[slot]; ++q) {
                         const float ca = T.pcoef_a[slot][q], cb = T.pcoef_b[slot][q];
+                        const bool sq = T.pfield[slot][q] < 0;
                         const float2* pr = wpt + np * WIN + r * M;
 #pragma unroll
                         for (int i = 0; i < E; ++i) {
-                            const float2 gv = pr[p + P * i];
+                            const float2 gv = sq ? x[i] : pr[p + P * i];
                             const float2 fg = lmul(x[i], gv);
                             accA[t][i] = lfma(ca, fg, accA[t][i]);
                             accB[t][i] = lfma(cb, fg, accB[t][i]);
                         }
+                        if (!sq) ++np;
                     }
                 }
             }
