@@ -35,7 +35,7 @@ FALLBACK_HBM_GBS = 6800.0
 # realisation of this workload (512^3); traffic per launch is reported as this
 # ratio times the launch's algorithmic bytes. A kernel changed since its
 # capture has no entry (traffic null).
-NCU_TRAFFIC_RATIO = {"y_expand": 1.025, "x_fwd_expand": 1.039}
+NCU_TRAFFIC_RATIO = {"z_expand": 1.008, "y_expand": 1.024, "x_fwd_expand": 1.039}
 
 
 def log_edges(lo, hi, nb):
