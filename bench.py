@@ -172,9 +172,19 @@ def oracle_sample(target_s=12.0, n=64, workers=1):
                                        f"IC + recursion, numpy FP64, {workers} process(es), {el:.1f} s"}
 
 
+def workload_config(n, batch, world):
+    """The `config` object of both arms' JSON lines (the workload, by its sizes)."""
+    L = BOX * n / N_GRID
+    return {"workload": f"gridspt-{n}^3-L{L:g}-nmax{N_MAX}", "grid": n, "box_mpc_h": L, "n_max": N_MAX,
+            "realisations_per_gpu": batch, "estimators": "6 P-terms x 32 log bins + B_tree x 16 shells",
+            "schedule": "recursion per realisation; its estimators on a second stream beside the next one",
+            "l2": "inputs larger than L2 (512 MiB fields), no flush", "parallelism": f"replicas{world}"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 oracle on all host cores, a bounded sample
-    of the workload per step."""
+    of the workload per step (the workload's `config`; the sample is described
+    in `cpu_baseline`)."""
     if rank != 0:
         return
     workers = os.cpu_count() or 1
@@ -192,8 +202,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "gridspt-64^3-L250-nmax5 (bounded oracle sample of "
-                                                        "gridspt-512^3-L2000-nmax5)"},
+            "data": "synthetic", "config": workload_config(args.n, args.batch, args.gpus),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -451,10 +460,7 @@ def run_gpu(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"gridspt-{N}^3-L{L:g}-nmax{N_MAX}", "grid": N, "box_mpc_h": L, "n_max": N_MAX,
-                   "realisations_per_gpu": B, "estimators": "6 P-terms x 32 log bins + B_tree x 16 shells",
-                   "schedule": "recursion per realisation; its estimators on a second stream beside the next one",
-                   "l2": "inputs larger than L2 (512 MiB fields), no flush", "parallelism": f"replicas{world}"},
+        "config": workload_config(N, B, world),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": (round(NCU_TRAFFIC_RATIO[kname] * kbytes / nl / 1e9, 3) if kname in NCU_TRAFFIC_RATIO
